@@ -1,0 +1,278 @@
+"""Pins for the FP64 oracle: each test checks the oracle against something
+other than itself (brute force, exact rational arithmetic, an independent
+Riccati solver, the paper's closed forms, invariants, finite differences).
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from pins import dense_kkt, riccati
+from workload import gen
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split(":", 1)
+            vals[k.strip()] = np.array([float(t) for t in v.split()])
+    return vals
+
+
+def _golden_lq():
+    g = _read_golden("scalar_two_knot.txt")
+    lq = gen.LQ(1, 1, 2, g["A"].reshape(1, 1, 1), g["B"].reshape(1, 1, 1),
+                g["Qd"].reshape(2, 1), g["Rd"].reshape(1, 1), g["q"].reshape(2, 1),
+                g["r"].reshape(1, 1), g["c"].reshape(2, 1))
+    return lq, g
+
+
+# ---------------------------------------------------------------- worked example
+def test_golden_scalar_two_knot_solution():
+    lq, g = _golden_lq()
+    lam, dx, du = oracle.kkt_solve(lq)
+    np.testing.assert_allclose(lam.ravel(), g["lam"], atol=1e-15)
+    np.testing.assert_allclose(dx.ravel(), g["dx"], atol=1e-15)
+    np.testing.assert_allclose(du.ravel(), g["du"], atol=1e-15)
+
+
+def test_golden_scalar_two_knot_blocks():
+    lq, g = _golden_lq()
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    np.testing.assert_allclose(Sd.ravel(), g["Sd"], atol=1e-15)
+    np.testing.assert_allclose(So.ravel(), g["So"], atol=1e-15)
+    np.testing.assert_allclose(gamma.ravel(), g["gamma"], atol=1e-15)
+    Pd, Po = oracle.precon_blocks(Sd, So)
+    np.testing.assert_allclose(Pd.ravel(), g["Pd"], atol=1e-15)
+    np.testing.assert_allclose(Po.ravel(), g["Po"], atol=1e-15)
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("nx,nu,N,seed", [(2, 1, 1, 0), (2, 1, 2, 1), (4, 2, 5, 2),
+                                          (14, 7, 8, 3), (36, 12, 3, 4), (6, 3, 8, 5)])
+def test_kkt_vs_dense_solve(nx, nu, N, seed):
+    lq = gen.kuka_lq(nx, nu, N, seed)
+    K, h, _ = dense_kkt(lq)
+    y = np.linalg.solve(K, h)
+    nz = N * nx + (N - 1) * nu
+    lam, dx, du = oracle.kkt_solve(lq)
+    np.testing.assert_allclose(lam.ravel(), y[nz:], rtol=0, atol=1e-10 * np.abs(y).max())
+    np.testing.assert_allclose(oracle.natural_z(dx, du), -y[:nz], rtol=0,
+                               atol=1e-10 * np.abs(y).max())
+
+
+def test_kkt_exact_rational():
+    """Exact rational solve of a small KKT system (no rounding anywhere)."""
+    sympy = pytest.importorskip("sympy")
+    rng = np.random.default_rng(11)
+    nx, nu, N = 2, 1, 3
+
+    def rat(lo, hi, shape):
+        return rng.integers(lo, hi, size=shape).astype(np.float64) / 4.0
+
+    lq = gen.LQ(nx, nu, N, rat(-4, 5, (N - 1, nx, nx)), rat(-4, 5, (N - 1, nx, nu)),
+                rat(1, 9, (N, nx)), rat(1, 9, (N - 1, nu)), rat(-8, 9, (N, nx)),
+                rat(-8, 9, (N - 1, nu)), rat(-8, 9, (N, nx)))
+    K, h, _ = dense_kkt(lq)
+    Ks = sympy.Matrix([[Fraction(v).limit_denominator() for v in row] for row in K])
+    hs = sympy.Matrix([Fraction(v).limit_denominator() for v in h])
+    y = np.array([float(v) for v in Ks.LUsolve(hs)])
+    nz = N * nx + (N - 1) * nu
+    lam, dx, du = oracle.kkt_solve(lq)
+    np.testing.assert_allclose(lam.ravel(), y[nz:], rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(oracle.natural_z(dx, du), -y[:nz], rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------- Riccati
+@pytest.mark.parametrize("nx,nu,N,seed,kw", [
+    (14, 7, 32, 1, {}),
+    (14, 7, 128, 130, {}),
+    (14, 7, 512, 514, {}),
+    (36, 12, 64, 5000, dict(dt=0.005, qd=(0.1, 100.0))),
+])
+def test_kkt_vs_riccati(nx, nu, N, seed, kw):
+    lq = gen.kuka_lq(nx, nu, N, seed, **kw)
+    lam, dx, du = oracle.kkt_solve(lq)
+    lr, xr, ur = riccati(lq)
+    assert oracle.relerr(lam, lr) < 1e-9
+    assert oracle.relerr(dx, xr) < 1e-9
+    assert oracle.relerr(du, ur) < 1e-9
+
+
+# ---------------------------------------------------------------- invariants
+@pytest.mark.parametrize("N,seed", [(32, 1), (128, 7)])
+def test_kkt_invariants(N, seed):
+    lq = gen.kuka_lq(14, 7, N, seed)
+    lam, dx, du = oracle.kkt_solve(lq)
+    # linearised dynamics C dz + c = 0
+    scale = max(1.0, np.abs(lq.c).max(), np.abs(dx).max() * (1 + np.abs(lq.A).max()))
+    res0 = dx[0] + lq.c[0]
+    resk = dx[1:] - np.einsum("kij,kj->ki", lq.A, dx[:-1]) - np.einsum("kij,kj->ki", lq.B, du) + lq.c[1:]
+    assert max(np.abs(res0).max(), np.abs(resk).max()) <= 1e-12 * scale * 10
+    # stationarity G dz + g - C^T lam = 0
+    sx = lq.Qd * dx + lq.q - lam
+    sx[:-1] += np.einsum("kji,kj->ki", lq.A, lam[1:])
+    su = lq.Rd * du + lq.r + np.einsum("kji,kj->ki", lq.B, lam[1:])
+    sc = max(1.0, np.abs(lam).max() * 10)
+    assert np.abs(sx).max() < 1e-11 * sc and np.abs(su).max() < 1e-11 * sc
+
+
+def test_schur_spd_and_precon_spd():
+    lq = gen.kuka_lq(14, 7, 24, 3)
+    Sd, So, _ = oracle.schur_blocks(lq)
+    S = oracle.block_tridiag_sparse(Sd, So).toarray()
+    np.linalg.cholesky(S)
+    Pd, Po = oracle.precon_blocks(Sd, So)
+    P = oracle.block_tridiag_sparse(Pd, Po).toarray()
+    assert np.abs(P - P.T).max() < 1e-12 * np.abs(P).max()
+    assert np.linalg.eigvalsh(P).min() > 0
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("nx,nu,N,seed", [(14, 7, 9, 21), (4, 2, 6, 22), (36, 12, 4, 23)])
+def test_schur_closed_forms(nx, nu, N, seed):
+    """schur_blocks (sparse C G^-1 C^T) against Eq. trajoptSchur_1/2."""
+    lq = gen.kuka_lq(nx, nu, N, seed)
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    Qi = [np.diag(1.0 / lq.Qd[k]) for k in range(N)]
+    Ri = [np.diag(1.0 / lq.Rd[k]) for k in range(N - 1)]
+    np.testing.assert_allclose(Sd[0], Qi[0], atol=1e-14)
+    np.testing.assert_allclose(gamma[0], lq.c[0] - Qi[0] @ lq.q[0], atol=1e-13)
+    for k in range(N - 1):
+        A, B = lq.A[k], lq.B[k]
+        theta = A @ Qi[k] @ A.T + B @ Ri[k] @ B.T + Qi[k + 1]
+        phi = -A @ Qi[k]
+        zeta = -A @ Qi[k] @ lq.q[k] - B @ Ri[k] @ lq.r[k] + Qi[k + 1] @ lq.q[k + 1]
+        np.testing.assert_allclose(Sd[k + 1], theta, rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(So[k], phi, rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(gamma[k + 1], lq.c[k + 1] - zeta, rtol=1e-12, atol=1e-12)
+
+
+def test_precon_matches_dense_formula_and_printed_blocks():
+    """Phi^-1 blocks against D^-1 - D^-1 O D^-1 (dense) and against the
+    blocks printed in Sec. IV-A for the first block rows."""
+    lq = gen.kuka_lq(6, 3, 7, 31)
+    Sd, So, _ = oracle.schur_blocks(lq)
+    Pd, Po = oracle.precon_blocks(Sd, So)
+    P = oracle.block_tridiag_sparse(Pd, Po).toarray()
+    Pdense = oracle.dense_Phi_inv(Sd, So)
+    np.testing.assert_allclose(P, Pdense, rtol=1e-12, atol=1e-12)
+    nx = 6
+    Q0 = np.diag(lq.Qd[0])
+    th0 = Sd[1]
+    th1 = Sd[2]
+    ph0, ph1 = So[0], So[1]
+    inv = np.linalg.inv
+    np.testing.assert_allclose(P[:nx, :nx], Q0, atol=1e-12)
+    np.testing.assert_allclose(P[:nx, nx:2 * nx], -Q0 @ ph0.T @ inv(th0), atol=1e-12)
+    np.testing.assert_allclose(P[nx:2 * nx, :nx], -inv(th0) @ ph0 @ Q0, atol=1e-12)
+    np.testing.assert_allclose(P[nx:2 * nx, nx:2 * nx], inv(th0), atol=1e-12)
+    np.testing.assert_allclose(P[nx:2 * nx, 2 * nx:3 * nx], -inv(th0) @ ph1.T @ inv(th1), atol=1e-12)
+    np.testing.assert_allclose(P[2 * nx:3 * nx, nx:2 * nx], -inv(th1) @ ph1 @ inv(th0), atol=1e-12)
+
+
+def test_schur_route_reaches_kkt_solution():
+    """Solving S+ lambda = -gamma then dz = -G^-1 (g - C^T lambda) gives the
+    KKT solution: pins schur_blocks, the sign reading and recover."""
+    lq = gen.kuka_lq(14, 7, 20, 41)
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    S = oracle.block_tridiag_sparse(Sd, So).toarray()
+    lam_s = np.linalg.solve(S, -gamma.ravel())
+    lam, dx, du = oracle.kkt_solve(lq)
+    assert oracle.relerr(lam_s, lam) < 1e-12
+    dx2, du2 = oracle.recover(lq, lam)
+    assert oracle.relerr(dx2, dx) < 1e-12 and oracle.relerr(du2, du) < 1e-12
+
+
+# ---------------------------------------------------------------- PCG special cases
+def test_pcg_reaches_kkt_solution():
+    lq = gen.kuka_lq(14, 7, 32, 1)
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    Pd, Po = oracle.precon_blocks(Sd, So)
+    lam_p, it, ok = oracle.pcg(Sd, So, Pd, Po, -gamma, tol=1e-12)
+    lam, _, _ = oracle.kkt_solve(lq)
+    assert ok and oracle.relerr(lam_p, lam) < 1e-9 and it > 10
+
+
+def test_pcg_decoupled_converges_in_one_iteration():
+    """A_k = B_k = 0: S+ is block diagonal and Phi^-1 = S+^-1 exactly."""
+    lq = gen.kuka_lq(14, 7, 16, 5)
+    lq.A[:] = 0.0
+    lq.B[:] = 0.0
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    Pd, Po = oracle.precon_blocks(Sd, So)
+    assert np.abs(Po).max() == 0.0
+    lam_p, it, ok = oracle.pcg(Sd, So, Pd, Po, -gamma, tol=1e-12)
+    assert ok and it == 1
+    lam, _, _ = oracle.kkt_solve(lq)
+    assert oracle.relerr(lam_p, lam) < 1e-13
+
+
+def test_pcg_identity_precon_is_textbook_cg():
+    """Phi = I reduces Algorithm 1 to plain CG: compare against scipy's CG."""
+    import scipy.sparse.linalg as spla
+    lq = gen.kuka_lq(4, 2, 10, 9)
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    I = np.broadcast_to(np.eye(4), Sd.shape).copy()
+    Z = np.zeros_like(So)
+    lam_p, it, ok = oracle.pcg(Sd, So, I, Z, -gamma, tol=1e-11)
+    S = oracle.block_tridiag_sparse(Sd, So)
+    x, info = spla.cg(S, -gamma.ravel(), rtol=1e-13, maxiter=10000)
+    assert ok and info == 0 and oracle.relerr(lam_p, x) < 1e-8
+
+
+def test_pcg_finite_termination():
+    """In exact arithmetic CG ends within n = N nx steps; in FP64 on a tiny
+    well-conditioned system it reaches 1e-12 by then."""
+    lq = gen.kuka_lq(2, 1, 4, 3)
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    Pd, Po = oracle.precon_blocks(Sd, So)
+    _, it, ok = oracle.pcg(Sd, So, Pd, Po, -gamma, tol=1e-12)
+    assert ok and it <= 8
+
+
+def test_pcg_warm_start_exact_takes_zero_iterations():
+    lq = gen.kuka_lq(4, 2, 6, 2)
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    Pd, Po = oracle.precon_blocks(Sd, So)
+    lam, _, _ = oracle.kkt_solve(lq)
+    _, it, ok = oracle.pcg(Sd, So, Pd, Po, -gamma, lam0=lam, tol=1e-8)
+    assert ok and it == 0
+
+
+# ---------------------------------------------------------------- gradient
+def test_grad_vs_central_differences():
+    """Analytic gradient (KKT adjoint) vs FP64 central differences, h = 1e-6,
+    on random coordinates of every parameter array."""
+    lq = gen.kuka_lq(6, 3, 6, 77)
+    w = gen.loss_weights(6 * 6, 4).reshape(6, 6)
+
+    def L(lq_):
+        lam, dx, du = oracle.kkt_solve(lq_)
+        return oracle.loss(lam, dx, du, w)
+
+    lam, dx, du = oracle.kkt_solve(lq)
+    g = oracle.grad(lq, lam, dx, du, w, 2 * dx, 2 * du)
+    rng = np.random.default_rng(4)
+    h = 1e-6
+    # central differences carry a rounding error of about eps |L| / h
+    round_err = 50 * np.finfo(np.float64).eps * abs(L(lq)) / h
+    for name in ("A", "B", "Qd", "Rd", "q", "r", "c"):
+        arr = getattr(lq, name)
+        for _ in range(8):
+            idx = tuple(rng.integers(0, s) for s in arr.shape)
+            p = lq.copy()
+            m = lq.copy()
+            getattr(p, name)[idx] += h
+            getattr(m, name)[idx] -= h
+            fd = (L(p) - L(m)) / (2 * h)
+            an = g[name][idx]
+            assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)) + round_err, (name, idx, fd, an)

@@ -1,0 +1,176 @@
+"""Seeded, synthetic, Kuka-shaped LQ subproblems (Sec. II-A, Step 1 output).
+
+The paper's measurements use the LQ subproblems produced inside 100 NMPC
+trials of a simulated Kuka IIWA-14 (Sec. V-A).  Those traces are not
+available, so every input here is drawn from a seeded generator with the
+same shapes (nx = 14 states = 7 joint positions + 7 velocities, nu = 7
+torques, 32..512 knot points) and a semi-implicit-Euler structure for the
+dynamics Jacobians:
+
+    A_k = [[I, dt I], [dt M_k, I + dt D_k]]       M_k, D_k ~ N(0, 0.5^2)
+    B_k = [[0], [dt (L_k L_k^T + 0.1 I)[:, :nu]]] L_k ~ N(0, 1), (nx/2)x(nx/2)
+    Qd_k ~ U[1, 10]   (diagonal of Q_k)      Rd_k ~ U[0.01, 0.1] (diag of R_k)
+    q_k, r_k, c_k ~ N(0, 1)
+
+Index convention: N is the number of knot points, i.e. the number of state
+blocks x_0..x_{N-1} and of block rows of the Schur complement; controls are
+u_0..u_{N-2}.  Array layouts (row-major, float64 master copies):
+
+    A[N-1][nx][nx]  B[N-1][nx][nu]  Qd[N][nx]  Rd[N-1][nu]
+    q[N][nx]        r[N-1][nu]      c[N][nx]
+
+Draw order per instance (numpy default_rng(seed)): M, Dm, L, Qd, Rd, q, r, c.
+No solver arithmetic lives here.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Sequence
+
+import numpy as np
+
+# Workload definitions (shapes, seeds, distributions) of the five measured
+# configurations.  Each is plain data.
+CONFIG_SMALL = dict(name="single-N32", nx=14, nu=7, N=32, seed=1, dt=0.01,
+                    qd=(1.0, 10.0))
+CONFIG_SWEEP = dict(name="sweep", nx=14, nu=7, Ns=(64, 128, 256, 512),
+                    seed_base=2, dt=0.01, qd=(1.0, 10.0), noise=0.01, reps=1000)
+CONFIG_BATCH = dict(name="batch256", nx=14, nu=7, B=256, N_lo=32, N_hi=512,
+                    n_seed=3, seed_base=1000, dt=0.01, qd=(1.0, 10.0),
+                    noise=0.01, solves=20)
+CONFIG_GRAD = dict(name="grad64", nx=14, nu=7, B=64, N=128, seed_base=4000,
+                   w_seed=4, dt=0.01, qd=(1.0, 10.0), fd_coords=50, fd_h=1e-6)
+CONFIG_LARGE = dict(name="large1024", nx=36, nu=12, B=1024, N_lo=64, N_hi=256,
+                    n_seed=5, seed_base=5000, dt=0.005, qd=(0.1, 100.0),
+                    noise=0.01, solves=10)
+
+
+@dataclass
+class LQ:
+    """One LQ subproblem; arrays in the layouts given in the module docstring."""
+    nx: int
+    nu: int
+    N: int
+    A: np.ndarray
+    B: np.ndarray
+    Qd: np.ndarray
+    Rd: np.ndarray
+    q: np.ndarray
+    r: np.ndarray
+    c: np.ndarray
+
+    FIELDS = ("A", "B", "Qd", "Rd", "q", "r", "c")
+
+    @property
+    def dtype(self):
+        return self.A.dtype
+
+    def astype(self, dt) -> "LQ":
+        kw = {f: np.ascontiguousarray(getattr(self, f), dtype=dt) for f in self.FIELDS}
+        return LQ(self.nx, self.nu, self.N, **kw)
+
+    def copy(self) -> "LQ":
+        kw = {f: np.array(getattr(self, f), copy=True) for f in self.FIELDS}
+        return LQ(self.nx, self.nu, self.N, **kw)
+
+
+def to_f32(lq: LQ) -> LQ:
+    """Round every array to float32 (the precision the GPU path stores)."""
+    return lq.astype(np.float32)
+
+
+def kuka_lq(nx: int, nu: int, N: int, seed: int, dt: float = 0.01,
+            qd=(1.0, 10.0), rd=(0.01, 0.1)) -> LQ:
+    """Draw one Kuka-shaped LQ subproblem (float64)."""
+    if nx % 2 or not (1 <= nu <= nx // 2) or N < 1:
+        raise ValueError("need even nx, 1 <= nu <= nx/2 and N >= 1")
+    h = nx // 2
+    K = max(N - 1, 0)
+    rng = np.random.default_rng(seed)
+    M = rng.normal(0.0, 0.5, size=(K, h, h))
+    Dm = rng.normal(0.0, 0.5, size=(K, h, h))
+    L = rng.normal(0.0, 1.0, size=(K, h, h))
+    Qd = rng.uniform(qd[0], qd[1], size=(N, nx))
+    Rd = rng.uniform(rd[0], rd[1], size=(K, nu))
+    q = rng.normal(0.0, 1.0, size=(N, nx))
+    r = rng.normal(0.0, 1.0, size=(K, nu))
+    c = rng.normal(0.0, 1.0, size=(N, nx))
+    eye = np.eye(h)
+    A = np.zeros((K, nx, nx))
+    A[:, :h, :h] = eye
+    A[:, :h, h:] = dt * eye
+    A[:, h:, :h] = dt * M
+    A[:, h:, h:] = eye + dt * Dm
+    Minv = np.einsum("kij,klj->kil", L, L) + 0.1 * eye
+    B = np.zeros((K, nx, nu))
+    B[:, h:, :] = dt * Minv[:, :, :nu]
+    return LQ(nx, nu, N, A, B, Qd, Rd, q, r, c)
+
+
+@dataclass
+class LQBatch:
+    """Many independent LQ subproblems with ragged horizons, concatenated.
+
+    knot_off[b] is the first knot of instance b in every per-knot array
+    (Qd, q, c and the per-knot outputs); the per-control arrays (A, B, Rd, r
+    and the off-diagonal outputs) of instance b start at knot_off[b] - b.
+    """
+    nx: int
+    nu: int
+    Ns: np.ndarray
+    knot_off: np.ndarray
+    lq: LQ                       # concatenated arrays; lq.N = total knots
+    items: List[LQ] = field(default_factory=list)
+
+    @property
+    def B(self) -> int:
+        return len(self.Ns)
+
+    def ctrl_off(self) -> np.ndarray:
+        return self.knot_off - np.arange(len(self.knot_off))
+
+    def astype(self, dt) -> "LQBatch":
+        return LQBatch(self.nx, self.nu, self.Ns.copy(), self.knot_off.copy(),
+                       self.lq.astype(dt), [it.astype(dt) for it in self.items])
+
+
+def concat_batch(items: Sequence[LQ]) -> LQBatch:
+    nx, nu = items[0].nx, items[0].nu
+    Ns = np.array([it.N for it in items], dtype=np.int64)
+    knot_off = np.zeros(len(items) + 1, dtype=np.int64)
+    knot_off[1:] = np.cumsum(Ns)
+    cat = {f: np.ascontiguousarray(np.concatenate([getattr(it, f) for it in items], axis=0))
+           for f in LQ.FIELDS}
+    lq = LQ(nx, nu, int(knot_off[-1]), **cat)
+    return LQBatch(nx, nu, Ns, knot_off, lq, list(items))
+
+
+def batch_horizons(B: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """Ragged horizons N_i ~ U{lo..hi} (inclusive)."""
+    return np.random.default_rng(seed).integers(lo, hi + 1, size=B)
+
+
+def kuka_batch(nx: int, nu: int, Ns: Sequence[int], seed_base: int, dt: float = 0.01,
+               qd=(1.0, 10.0)) -> LQBatch:
+    items = [kuka_lq(nx, nu, int(n), seed_base + i, dt=dt, qd=qd) for i, n in enumerate(Ns)]
+    return concat_batch(items)
+
+
+def warm_noise(seed: int, rep: int, shape) -> np.ndarray:
+    """Standard-normal draws for repetition `rep` of instance `seed`."""
+    return np.random.default_rng([seed, rep]).normal(0.0, 1.0, size=shape)
+
+
+def warm_start(lam_star: np.ndarray, seed: int, rep: int, rel: float = 0.01) -> np.ndarray:
+    """Perturbed warm start lam0 = lam_star * (1 + rel * xi), xi ~ N(0, 1).
+
+    Mimics the previous SQP iteration's multipliers (Sec. IV-B, last
+    sentences): a nearby but not converged starting point.
+    """
+    xi = warm_noise(seed, rep, lam_star.shape)
+    return (lam_star * (1.0 + rel * xi)).astype(lam_star.dtype)
+
+
+def loss_weights(n_lam: int, seed: int) -> np.ndarray:
+    """w ~ N(0, 1) for the scalar loss sum ||dz||^2 + w^T lambda."""
+    return np.random.default_rng(seed).normal(0.0, 1.0, size=n_lam)
