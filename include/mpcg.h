@@ -1,0 +1,217 @@
+/*
+ * mpcg.h -- C ABI of the GB300 (sm_103a) Schur-complement PCG solve path
+ * for the KKT systems of direct trajectory optimisation (MPCGPU, arXiv
+ * 2309.08079).
+ *
+ * The path (Sec. IV of the paper):
+ *   mpcg_form_schur    S+ = C G^-1 C^T and gamma          (Sec. II-B, Eq. schur,
+ *                                                          Eq. trajoptSchur_1/2)
+ *   mpcg_form_precon   symmetric stair preconditioner     (Sec. IV-A)
+ *   mpcg_pcg_solve     PCG on S+ lambda = -gamma          (Algorithm 1; the
+ *                                                          per-block form of
+ *                                                          Algorithm 2)
+ *   mpcg_recover_step  dz = -G^-1 (g - C^T lambda)        (Eq. schur)
+ * plus two additions with no counterpart in the paper: batched (ragged
+ * horizon) forms of every call and a backward (adjoint) pass.
+ *
+ * Problem statement (Sec. II-A, Step 2).  N knot points, states
+ * x_0..x_{N-1} (nx each), controls u_0..u_{N-2} (nu each).  G is diagonal:
+ * G = diag(Qd_0, Rd_0, Qd_1, ..., Qd_{N-1}).  C has I in block row 0 and
+ * [-A_k  -B_k  I] on (x_k, u_k, x_{k+1}) in block row k+1.
+ *
+ * Sign convention.  The paper writes S = -C G^-1 C^T, S lambda = gamma.
+ * This library stores the positive definite S+ = C G^-1 C^T and solves
+ * S+ lambda = -gamma, which has the same solution lambda.
+ *
+ * Conventions for every call:
+ *  - All array arguments are DEVICE pointers owned by the caller, dense,
+ *    row-major, of the element type named by dims.dtype (0 = float32,
+ *    1 = float64).  Layouts (per instance):
+ *        A[N-1][nx][nx]   B[N-1][nx][nu]   Qd[N][nx]   Rd[N-1][nu]
+ *        q[N][nx]         r[N-1][nu]       c[N][nx]
+ *        Sd[N][nx][nx]    diagonal blocks of S+ (D_0 = Qd_0^-1, D_{k+1} = theta_k)
+ *        So[N-1][nx][nx]  So[k] = block (k+1, k) of S+ = phi_k = -A_k Q_k^-1
+ *        Pd[N][nx][nx]    diagonal blocks of Phi^-1 (D_k^-1)
+ *        Po[N-1][nx][nx]  Po[k] = block (k+1, k) of Phi^-1 = -Pd[k+1] So[k] Pd[k]
+ *        gamma[N][nx]     gamma = c - C G^-1 g
+ *        lambda[N][nx]    dx[N][nx]   du[N-1][nu]
+ *  - Calls are asynchronous and ordered on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream).  They allocate no memory.  Calls made on one
+ *    handle from several host threads at once must use different handles.
+ *  - The return value reports argument and launch errors synchronously
+ *    (MPCG_OK, MPCG_EINVAL, MPCG_ECUDA, MPCG_EUNSUPPORTED).  Numerical
+ *    outcomes are written to device memory (mpcg_stats.status, info words).
+ *  - Batched calls take `knot_off`, a DEVICE int array of B+1 entries:
+ *    instance b owns knots knot_off[b] .. knot_off[b+1]-1 of every per-knot
+ *    array and entries knot_off[b]-b .. knot_off[b+1]-b-2 of every
+ *    per-control array (A, B, Rd, r, So, Po, du).  dims.N is then the LARGEST
+ *    horizon in the batch (used to size launches) and every N_b >= 1.
+ */
+#ifndef MPCG_H
+#define MPCG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes (negative: never equal to a status code) */
+#define MPCG_OK 0
+#define MPCG_EINVAL (-1)       /* bad argument (null pointer, size, dtype) */
+#define MPCG_ECUDA (-2)        /* a CUDA runtime call or launch failed */
+#define MPCG_EUNSUPPORTED (-3) /* shape outside what the kernels support */
+
+/* numerical status written to mpcg_stats.status */
+#define MPCG_CONVERGED 0
+#define MPCG_NOT_CONVERGED 1 /* max_iter reached; lambda holds the last iterate */
+#define MPCG_BREAKDOWN 2     /* p^T S+ p <= 0 or not finite */
+#define MPCG_NONFINITE 3     /* a residual or preconditioned residual is not finite */
+#define MPCG_BADINPUT 4      /* form_schur found Qd or Rd <= 0 or not finite */
+#define MPCG_TIMEOUT 5       /* a bounded device wait gave up (never expected) */
+
+/* info bits written by mpcg_form_schur into mpcg_schur.info[b] */
+#define MPCG_INFO_BADINPUT 1u
+
+typedef struct {
+    int nx, nu, N; /* N: horizon (batched calls: largest horizon) */
+    int dtype;     /* 0 = float32, 1 = float64 */
+} mpcg_dims;
+
+typedef struct {
+    const void *A, *B, *Qd, *Rd, *q, *r, *c;
+} mpcg_lq;
+
+typedef struct {
+    void *Sd, *So, *Pd, *Po, *gamma;
+    unsigned int *info; /* device, one word per instance, or NULL */
+} mpcg_schur;
+
+typedef struct {
+    double tol;    /* exit tolerance (<= 0: 1e-6) */
+    int tol_mode;  /* 0: ||r||_2 <= tol ||b||_2 (recurrence residual);
+                      1: paper's eta' = r^T Phi^-1 r < tol (Algorithm 1) */
+    int max_iter;  /* <= 0: 10 N nx */
+    int cluster;   /* CTAs per instance (1..16); 0 = automatic */
+    int reserved;
+} mpcg_opts;
+
+typedef struct {
+    int iters;     /* PCG iterations performed */
+    int status;    /* MPCG_CONVERGED, ... */
+    double eta;    /* final r^T Phi^-1 r */
+    double relres; /* final ||r||_2 / ||b||_2 (recurrence residual) */
+} mpcg_stats;
+
+typedef struct {
+    void *A, *B, *Qd, *Rd, *q, *r, *c; /* gradients, input layouts */
+} mpcg_grads;
+
+typedef struct mpcg_handle mpcg_handle;
+
+/* Library version as "major.minor.patch". */
+const char *mpcg_version(void);
+
+/* Message for a return code (< 0 or MPCG_OK) or a status code (>= 0); never NULL. */
+const char *mpcg_strerror(int code);
+
+/*
+ * Create a handle bound to the CUDA device current on the calling thread.
+ * Queries the device (SM count, cluster limits) and sets the kernels'
+ * launch attributes once.  Returns MPCG_ECUDA if no device is usable.
+ */
+int mpcg_create(mpcg_handle **out);
+void mpcg_destroy(mpcg_handle *h);
+
+/*
+ * Bytes of device workspace the batched and backward calls need for a
+ * batch of B instances with the given dims (single-instance calls need
+ * none and accept NULL).  The workspace is caller-owned and may be reused
+ * across calls that do not overlap on the GPU.
+ */
+size_t mpcg_workspace_bytes(mpcg_dims dims, int B);
+
+/*
+ * S+ and gamma, one block row per knot (Sec. II-B, Eq. trajoptSchur_1/2):
+ *   theta_k = A_k Q_k^-1 A_k^T + B_k R_k^-1 B_k^T + Q_{k+1}^-1
+ *   phi_k   = -A_k Q_k^-1
+ *   zeta_k  = -A_k Q_k^-1 q_k - B_k R_k^-1 r_k + Q_{k+1}^-1 q_{k+1}
+ * Writes Sd, So, gamma.  If schur->info is not NULL it is cleared and
+ * MPCG_INFO_BADINPUT is set when any Qd or Rd entry is <= 0 or not finite.
+ */
+int mpcg_form_schur(mpcg_handle *h, mpcg_dims dims, const mpcg_lq *lq, mpcg_schur *schur,
+                    void *stream);
+
+/*
+ * Symmetric stair preconditioner (Sec. IV-A): Pd[k] = Sd[k]^-1 (Gauss-Jordan,
+ * symmetrised) and Po[k] = -Pd[k+1] So[k] Pd[k].  Reads Sd, So; writes Pd, Po.
+ */
+int mpcg_form_precon(mpcg_handle *h, mpcg_dims dims, mpcg_schur *schur, void *stream);
+
+/*
+ * PCG (Algorithm 1) on S+ lambda = -gamma with preconditioner Phi^-1, in one
+ * persistent launch.  `lambda` is read as the warm start lambda_0 and
+ * overwritten with the result.  `stats` is a DEVICE pointer (one entry)
+ * written at exit.  `opts` is a HOST pointer (NULL: defaults).  Dot
+ * products are accumulated beyond the storage precision (float32 pairs for
+ * dtype 0, float64 for dtype 1).  If schur->info flags bad input, lambda is
+ * left unchanged and stats->status = MPCG_BADINPUT.
+ */
+int mpcg_pcg_solve(mpcg_handle *h, mpcg_dims dims, const mpcg_schur *schur, void *lambda,
+                   const mpcg_opts *opts, mpcg_stats *stats, void *stream);
+
+/*
+ * Primal step (Eq. schur): dz = -G^-1 (g - C^T lambda), i.e.
+ *   dx_k = (lambda_k - A_k^T lambda_{k+1} - q_k) / Qd_k   (k < N-1)
+ *   dx_{N-1} = (lambda_{N-1} - q_{N-1}) / Qd_{N-1}
+ *   du_k = (-B_k^T lambda_{k+1} - r_k) / Rd_k
+ */
+int mpcg_recover_step(mpcg_handle *h, mpcg_dims dims, const mpcg_lq *lq, const void *lambda,
+                      void *dx, void *du, void *stream);
+
+/* Batched forms: B independent instances in one launch each (see knot_off
+ * above).  Stats has B entries; pcg_solve_batched needs a workspace of
+ * mpcg_workspace_bytes(dims, B) bytes (its instance queue). */
+int mpcg_form_schur_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
+                            const mpcg_lq *lq, mpcg_schur *schur, void *stream);
+int mpcg_form_precon_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
+                             mpcg_schur *schur, void *stream);
+int mpcg_pcg_solve_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
+                           const mpcg_schur *schur, void *lambda, const mpcg_opts *opts,
+                           mpcg_stats *stats, void *workspace, void *stream);
+int mpcg_recover_step_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
+                              const mpcg_lq *lq, const void *lambda, void *dx, void *du,
+                              void *stream);
+
+/*
+ * Backward pass (no counterpart in the paper).  Given the forward inputs,
+ * the S+ / Phi^-1 built by the forward, its solution (lambda, dx, du) and
+ * the loss gradients lam_bar = dL/dlambda, dx_bar = dL/ddx, du_bar =
+ * dL/ddu, computes dL/d(A, B, Qd, Rd, q, r, c) into `grads`:
+ *   seed      lambda_bar' = lam_bar + C G^-1 (dx_bar, du_bar)
+ *   adjoint   S+ mu = lambda_bar'  (PCG with the same Phi^-1)
+ *   g_bar     = G^-1 (C^T mu - (dx_bar, du_bar))
+ *   Qd_bar = g_bar_x * dx, Rd_bar = g_bar_u * du, q_bar = g_bar_x,
+ *   r_bar = g_bar_u, c_bar = -mu,
+ *   A_bar_k = mu_{k+1} dx_k^T + lambda_{k+1} g_bar_x_k^T,
+ *   B_bar_k = mu_{k+1} du_k^T + lambda_{k+1} g_bar_u_k^T.
+ * `workspace` needs mpcg_workspace_bytes(dims, B) bytes (holds lambda_bar'
+ * and mu).  `stats` (device, B entries) receives the adjoint solve's stats.
+ * The _batched form takes knot_off as above; the plain form is B = 1 with
+ * knot_off = NULL.
+ */
+int mpcg_backward_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
+                          const mpcg_lq *lq, const mpcg_schur *schur, const void *lambda,
+                          const void *dx, const void *du, const void *lam_bar,
+                          const void *dx_bar, const void *du_bar, const mpcg_grads *grads,
+                          const mpcg_opts *opts, mpcg_stats *stats, void *workspace,
+                          void *stream);
+int mpcg_backward(mpcg_handle *h, mpcg_dims dims, const mpcg_lq *lq, const mpcg_schur *schur,
+                  const void *lambda, const void *dx, const void *du, const void *lam_bar,
+                  const void *dx_bar, const void *du_bar, const mpcg_grads *grads,
+                  const mpcg_opts *opts, mpcg_stats *stats, void *workspace, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPCG_H */

@@ -1,0 +1,346 @@
+// C ABI of the solve path (include/mpcg.h): argument checks, launch-shape
+// selection and stream-ordered launches.  No call allocates memory.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <type_traits>
+
+#include "launch.cuh"
+
+
+using namespace mpcg;
+
+struct mpcg_handle {
+    int device = 0;
+    int sms = 0;
+    int smem_optin = 0;
+    std::mutex mu;
+    // launch shapes already chosen: (dtype, nx, N, B, requested cluster) -> shape
+    std::map<std::tuple<int, int, int, int, int>, PcgLaunch> shapes;
+};
+
+namespace {
+
+constexpr int kMaxThreads = 512;
+constexpr int kMaxCluster = 16;
+
+inline int err_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return MPCG_OK;
+    std::fprintf(stderr, "mpcg: CUDA error %d (%s)\n", (int)e, cudaGetErrorString(e));
+    cudaGetLastError();  // a launch error is not sticky: do not leave it for the caller's next call
+    return MPCG_ECUDA;
+}
+
+inline bool dims_ok(const mpcg_dims &d) {
+    return d.nx >= 1 && d.nu >= 1 && d.N >= 1 && (d.dtype == 0 || d.dtype == 1);
+}
+
+inline size_t esize(const mpcg_dims &d) { return d.dtype == 1 ? 8 : 4; }
+inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+BatchView make_bv(const int *knot_off, int B, int N) {
+    BatchView bv;
+    bv.knot_off = knot_off;
+    bv.B = B;
+    bv.N1 = N;
+    return bv;
+}
+
+// Launch shape of the PCG kernel for horizons up to Nmax.
+template <typename T>
+int choose_pcg(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, PcgLaunch &L) {
+    const int nx = d.nx;
+    const bool reg = std::is_same<T, float>::value && nx == 14;
+    int max_threads = kMaxThreads;
+    if (reg) { L.lpk = 8; L.rpt = 2; max_threads = 256; }  // 2 register-resident rows per thread
+    else if (nx <= 16) { L.lpk = 16; L.rpt = 1; }
+    else if (nx <= 32) { L.lpk = 32; L.rpt = 1; }
+    else if (nx <= 64) { L.lpk = 32; L.rpt = 2; }
+    else return MPCG_EUNSUPPORTED;
+    const int kpc_cap = max_threads / L.lpk;  // knot slots per CTA
+    int C = (o && o->cluster > 0) ? o->cluster : ceil_div(d.N, kpc_cap);
+    if (C > kMaxCluster) return MPCG_EUNSUPPORTED;
+    C = std::max(1, std::min(C, d.N));
+    for (;;) {
+        L.C = C;
+        L.kpc_max = ceil_div(d.N, C);
+        if (L.kpc_max > kpc_cap) return MPCG_EUNSUPPORTED;
+        L.threads = std::max(32, ceil_div(L.kpc_max * L.lpk, 32) * 32);
+        L.mode = reg ? MODE_REG : MODE_PTR;
+        L.vs = nx <= 16 ? 16 : ceil_div(nx, 4) * 4;
+        const int W = L.threads / 32;
+        L.stage = 0;
+        if (L.mode == MODE_PTR) {
+            size_t with = pcg_smem_bytes<T>(L.kpc_max, L.vs, C, W, nx, 1);
+            if (with <= (size_t)h->smem_optin) L.stage = 1;
+        }
+        L.smem = pcg_smem_bytes<T>(L.kpc_max, L.vs, C, W, nx, L.stage);
+        const int active = pcg_max_clusters<T>(L);
+        if (active >= 1) {
+            L.clusters = std::max(1, std::min(B, active));
+            return MPCG_OK;
+        }
+        // this cluster size cannot be co-scheduled: try a smaller one
+        if (o && o->cluster > 0) return MPCG_EUNSUPPORTED;
+        if (C <= 1 || ceil_div(d.N, C / 2) > kpc_cap) return MPCG_EUNSUPPORTED;
+        C = C / 2;
+    }
+}
+
+template <typename T>
+int form_schur_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const mpcg_lq *lq,
+                 mpcg_schur *s, cudaStream_t st) {
+    SchurArgs<T> a;
+    a.nx = d.nx;
+    a.nu = d.nu;
+    a.bv = make_bv(knot_off, B, d.N);
+    a.Kgrid = knot_off ? B * d.N : d.N;
+    a.A = (const T *)lq->A; a.B = (const T *)lq->B; a.Qd = (const T *)lq->Qd;
+    a.Rd = (const T *)lq->Rd; a.q = (const T *)lq->q; a.r = (const T *)lq->r;
+    a.c = (const T *)lq->c;
+    a.Sd = (T *)s->Sd; a.So = (T *)s->So; a.gamma = (T *)s->gamma;
+    a.info = s->info;
+    if (s->info) {
+        int e = err_cuda(cudaMemsetAsync(s->info, 0, sizeof(unsigned) * B, st));
+        if (e) return e;
+    }
+    return err_cuda(launch_form_schur<T>(a, st));
+}
+
+template <typename T>
+int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const mpcg_schur *s,
+          const T *rhs, T sign, T *lam, const mpcg_opts *o, mpcg_stats *stats, void *ws,
+          cudaStream_t st) {
+    PcgLaunch L;
+    int rc = MPCG_OK;
+    {
+        std::lock_guard<std::mutex> g(h->mu);
+        auto key = std::make_tuple(d.dtype, d.nx, d.N, B, o ? o->cluster : 0);
+        auto it = h->shapes.find(key);
+        if (it != h->shapes.end()) {
+            L = it->second;
+        } else {
+            rc = choose_pcg<T>(h, d, B, o, L);
+            if (rc == MPCG_OK) h->shapes.emplace(key, L);
+        }
+    }
+    if (rc) return rc;
+    PcgParams<T> P;
+    P.nx = d.nx;
+    P.bv = make_bv(knot_off, B, d.N);
+    P.Sd = (const T *)s->Sd; P.So = (const T *)s->So;
+    P.Pd = (const T *)s->Pd; P.Po = (const T *)s->Po;
+    P.rhs = rhs;
+    P.rhs_sign = sign;
+    P.lam = lam;
+    P.info = s->info;
+    P.stats = stats;
+    P.queue = nullptr;
+    P.tol = o ? o->tol : 1e-6;
+    P.tol_mode = o ? o->tol_mode : 0;
+    P.max_iter = o ? o->max_iter : 0;
+    if (B > 1 && L.clusters < B) {
+        if (!ws) return MPCG_EINVAL;
+        P.queue = (int *)ws;
+        rc = err_cuda(cudaMemsetAsync(ws, 0, sizeof(int), st));
+        if (rc) return rc;
+    }
+    return err_cuda(pcg_launch<T>(L, P, st));
+}
+
+template <typename T>
+int backward_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const mpcg_lq *lq,
+               const mpcg_schur *s, const T *lam, const T *dx, const T *du, const T *lam_bar,
+               const T *dx_bar, const T *du_bar, const mpcg_grads *g, const mpcg_opts *o,
+               mpcg_stats *stats, void *ws, cudaStream_t st) {
+    BatchView bv = make_bv(knot_off, B, d.N);
+    const int Kgrid = knot_off ? B * d.N : d.N;
+    const size_t vec = al256((size_t)Kgrid * d.nx * sizeof(T));
+    char *w = (char *)ws;
+    T *lbar = (T *)(w + 256);
+    T *mu = (T *)(w + 256 + vec);
+    const T *A = (const T *)lq->A, *Bm = (const T *)lq->B, *Qd = (const T *)lq->Qd,
+            *Rd = (const T *)lq->Rd;
+    int rc = err_cuda(launch_cgh<T>(d.nx, d.nu, bv, Kgrid, A, Bm, Qd, Rd, dx_bar, du_bar, lam_bar,
+                                    lbar, st));
+    if (rc) return rc;
+    rc = err_cuda(cudaMemsetAsync(mu, 0, (size_t)Kgrid * d.nx * sizeof(T), st));
+    if (rc) return rc;
+    rc = pcg_t<T>(h, d, B, knot_off, s, lbar, T(1), mu, o, stats, ws, st);
+    if (rc) return rc;
+    rc = err_cuda(launch_recover<T>(d.nx, d.nu, bv, Kgrid, A, Bm, Qd, Rd, dx_bar, du_bar, mu,
+                                    (T *)g->q, (T *)g->r, st));
+    if (rc) return rc;
+    return err_cuda(launch_grad<T>(d.nx, d.nu, bv, Kgrid, lam, mu, dx, du, (const T *)g->q,
+                                   (const T *)g->r, (T *)g->A, (T *)g->B, (T *)g->Qd, (T *)g->Rd,
+                                   (T *)g->c, st));
+}
+
+template <typename T>
+int precon_t(const mpcg_dims &d, int B, const int *knot_off, mpcg_schur *s, cudaStream_t st) {
+    return err_cuda(launch_form_precon<T>(d.nx, make_bv(knot_off, B, d.N), knot_off ? B * d.N : d.N,
+                                          (const T *)s->Sd, (const T *)s->So, (T *)s->Pd,
+                                          (T *)s->Po, st));
+}
+
+template <typename T>
+int solve_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off,
+                   const mpcg_schur *s, void *lam, const mpcg_opts *o, mpcg_stats *stats, void *ws,
+                   cudaStream_t st) {
+    return pcg_t<T>(h, d, B, knot_off, s, (const T *)s->gamma, T(-1), (T *)lam, o, stats, ws, st);
+}
+
+template <typename T>
+int recover_t(const mpcg_dims &d, int B, const int *knot_off, const mpcg_lq *lq,
+                     const void *lam, void *dx, void *du, cudaStream_t st) {
+    return err_cuda(launch_recover<T>(d.nx, d.nu, make_bv(knot_off, B, d.N),
+                                      knot_off ? B * d.N : d.N, (const T *)lq->A,
+                                      (const T *)lq->B, (const T *)lq->Qd, (const T *)lq->Rd,
+                                      (const T *)lq->q, (const T *)lq->r, (const T *)lam, (T *)dx,
+                                      (T *)du, st));
+}
+
+// Per-control arrays (A, B, Rd, r) are empty, and may be NULL, when every
+// horizon is 1 (dims.N == 1).
+bool lq_ok(const mpcg_lq *lq, const mpcg_dims &d) {
+    if (!lq || !lq->Qd || !lq->q || !lq->c) return false;
+    return d.N == 1 || (lq->A && lq->B && lq->Rd && lq->r);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mpcg_version(void) { return "0.1.0"; }
+
+const char *mpcg_strerror(int code) {
+    switch (code) {
+        case MPCG_OK: return "ok (converged)";
+        case MPCG_EINVAL: return "invalid argument";
+        case MPCG_ECUDA: return "CUDA runtime or launch error";
+        case MPCG_EUNSUPPORTED: return "shape not supported by the kernels";
+        case MPCG_NOT_CONVERGED: return "not converged within max_iter";
+        case MPCG_BREAKDOWN: return "breakdown: p^T S p <= 0 or not finite";
+        case MPCG_NONFINITE: return "residual not finite";
+        case MPCG_BADINPUT: return "bad input: Qd or Rd not positive and finite";
+        case MPCG_TIMEOUT: return "bounded device wait gave up";
+        default: return "unknown code";
+    }
+}
+
+int mpcg_create(mpcg_handle **out) {
+    if (!out) return MPCG_EINVAL;
+    *out = nullptr;
+    mpcg_handle *h = new mpcg_handle();
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return MPCG_ECUDA;
+    }
+    if (pcg_prepare(h->smem_optin) != cudaSuccess || form_prepare(h->smem_optin) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return MPCG_ECUDA;
+    }
+    *out = h;
+    return MPCG_OK;
+}
+
+void mpcg_destroy(mpcg_handle *h) { delete h; }
+
+size_t mpcg_workspace_bytes(mpcg_dims d, int B) {
+    if (!dims_ok(d) || B < 1) return 0;
+    const size_t vec = al256((size_t)B * d.N * d.nx * esize(d));
+    return 256 + 2 * vec;
+}
+
+#define DISPATCH(d, F, ...) ((d).dtype == 1 ? F<double>(__VA_ARGS__) : F<float>(__VA_ARGS__))
+
+int mpcg_form_schur_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,
+                            const mpcg_lq *lq, mpcg_schur *s, void *stream) {
+    if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !s->Sd ||
+        (!s->So && d.N > 1) || !s->gamma)
+        return MPCG_EINVAL;
+    return DISPATCH(d, form_schur_t, h, d, B, knot_off, lq, s, (cudaStream_t)stream);
+}
+
+int mpcg_form_schur(mpcg_handle *h, mpcg_dims d, const mpcg_lq *lq, mpcg_schur *s, void *stream) {
+    return mpcg_form_schur_batched(h, d, 1, nullptr, lq, s, stream);
+}
+
+int mpcg_form_precon_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off, mpcg_schur *s,
+                             void *stream) {
+    if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !s || !s->Sd || !s->Pd ||
+        (d.N > 1 && (!s->So || !s->Po)))
+        return MPCG_EINVAL;
+    return DISPATCH(d, precon_t, d, B, knot_off, s, (cudaStream_t)stream);
+}
+
+int mpcg_form_precon(mpcg_handle *h, mpcg_dims d, mpcg_schur *s, void *stream) {
+    return mpcg_form_precon_batched(h, d, 1, nullptr, s, stream);
+}
+
+int mpcg_pcg_solve_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,
+                           const mpcg_schur *s, void *lambda, const mpcg_opts *opts,
+                           mpcg_stats *stats, void *workspace, void *stream) {
+    if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !s || !s->Sd || !s->Pd ||
+        (d.N > 1 && (!s->So || !s->Po)) || !s->gamma || !lambda)
+        return MPCG_EINVAL;
+    return DISPATCH(d, solve_t, h, d, B, knot_off, s, lambda, opts, stats, workspace,
+                    (cudaStream_t)stream);
+}
+
+int mpcg_pcg_solve(mpcg_handle *h, mpcg_dims d, const mpcg_schur *s, void *lambda,
+                   const mpcg_opts *opts, mpcg_stats *stats, void *stream) {
+    return mpcg_pcg_solve_batched(h, d, 1, nullptr, s, lambda, opts, stats, nullptr, stream);
+}
+
+int mpcg_recover_step_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,
+                              const mpcg_lq *lq, const void *lambda, void *dx, void *du,
+                              void *stream) {
+    if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !lambda || !dx ||
+        (!du && d.N > 1))
+        return MPCG_EINVAL;
+    return DISPATCH(d, recover_t, d, B, knot_off, lq, lambda, dx, du, (cudaStream_t)stream);
+}
+
+int mpcg_recover_step(mpcg_handle *h, mpcg_dims d, const mpcg_lq *lq, const void *lambda, void *dx,
+                      void *du, void *stream) {
+    return mpcg_recover_step_batched(h, d, 1, nullptr, lq, lambda, dx, du, stream);
+}
+
+int mpcg_backward_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,
+                          const mpcg_lq *lq, const mpcg_schur *s, const void *lambda,
+                          const void *dx, const void *du, const void *lam_bar, const void *dx_bar,
+                          const void *du_bar, const mpcg_grads *g, const mpcg_opts *opts,
+                          mpcg_stats *stats, void *workspace, void *stream) {
+    if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !lambda || !dx ||
+        !lam_bar || !dx_bar || !g || !g->A || !g->B || !g->Qd || !g->Rd || !g->q || !g->r ||
+        !g->c || !workspace || (d.N > 1 && (!du || !du_bar)))
+        return MPCG_EINVAL;
+    if (d.dtype == 1)
+        return backward_t<double>(h, d, B, knot_off, lq, s, (const double *)lambda,
+                                  (const double *)dx, (const double *)du, (const double *)lam_bar,
+                                  (const double *)dx_bar, (const double *)du_bar, g, opts, stats,
+                                  workspace, (cudaStream_t)stream);
+    return backward_t<float>(h, d, B, knot_off, lq, s, (const float *)lambda, (const float *)dx,
+                             (const float *)du, (const float *)lam_bar, (const float *)dx_bar,
+                             (const float *)du_bar, g, opts, stats, workspace,
+                             (cudaStream_t)stream);
+}
+
+int mpcg_backward(mpcg_handle *h, mpcg_dims d, const mpcg_lq *lq, const mpcg_schur *s,
+                  const void *lambda, const void *dx, const void *du, const void *lam_bar,
+                  const void *dx_bar, const void *du_bar, const mpcg_grads *g,
+                  const mpcg_opts *opts, mpcg_stats *stats, void *workspace, void *stream) {
+    return mpcg_backward_batched(h, d, 1, nullptr, lq, s, lambda, dx, du, lam_bar, dx_bar, du_bar,
+                                 g, opts, stats, workspace, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,269 @@
+// Device utilities shared by the mpcg kernels: extended-precision
+// accumulators, thread-block-cluster primitives (inline PTX, sm_90+ ISA,
+// compiled for sm_103a) and instance bookkeeping for ragged batches.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mpcg.h"
+
+namespace mpcg {
+
+// ---------------------------------------------------------------------------
+// Accumulators.  GB300's FP64 pipe runs at a small fraction of its FP32 rate,
+// so float32 dot products are accumulated as unevaluated float pairs
+// (hi + lo, "double-float"): the product of two floats is split exactly with
+// one FMA, and pairs are added with Knuth's TwoSum.  Both operations are
+// exact transformations, commutative in their operands, and give about 44
+// significant bits.  The float64 path accumulates in plain double.
+// ---------------------------------------------------------------------------
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return dfloat{p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ dfloat df_add(dfloat x, dfloat y) {
+    float s = __fadd_rn(x.hi, y.hi);
+    float bb = __fsub_rn(s, x.hi);
+    float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
+    float hi = __fadd_rn(s, e);
+    return dfloat{hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+
+// Tree form of the pair addition: the high parts are added with TwoSum and
+// the rounding error is carried into the low part without renormalising.
+// Exact in the high part, commutative, and about 35% shorter on the
+// dependency chain than df_add; used for shuffle and slot reductions.
+__device__ __forceinline__ dfloat df_add_lazy(dfloat a, dfloat b) {
+    float s = __fadd_rn(a.hi, b.hi);
+    float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    return dfloat{s, __fadd_rn(__fadd_rn(a.lo, b.lo), e)};
+}
+
+template <typename T>
+struct Acc;
+
+template <>
+struct Acc<float> {
+    using type = dfloat;
+    __device__ static __forceinline__ dfloat zero() { return dfloat{0.f, 0.f}; }
+    __device__ static __forceinline__ dfloat prod(float a, float b) { return df_prod(a, b); }
+    __device__ static __forceinline__ dfloat add(dfloat a, dfloat b) { return df_add(a, b); }
+    __device__ static __forceinline__ dfloat add_tree(dfloat a, dfloat b) { return df_add_lazy(a, b); }
+    __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    __device__ static __forceinline__ dfloat shfl_xor(dfloat a, int m) {
+        return dfloat{__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+    }
+    __device__ static __forceinline__ dfloat bcast0(dfloat a) {
+        return dfloat{__shfl_sync(0xffffffffu, a.hi, 0), __shfl_sync(0xffffffffu, a.lo, 0)};
+    }
+    __device__ static __forceinline__ double to_double(dfloat a) {
+        return (double)a.hi + (double)a.lo;
+    }
+    __device__ static __forceinline__ float to_T(dfloat a) { return __fadd_rn(a.hi, a.lo); }
+};
+
+template <>
+struct Acc<double> {
+    using type = double;
+    __device__ static __forceinline__ double zero() { return 0.0; }
+    __device__ static __forceinline__ double prod(double a, double b) { return __dmul_rn(a, b); }
+    __device__ static __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ static __forceinline__ double add_tree(double a, double b) { return __dadd_rn(a, b); }
+    __device__ static __forceinline__ double div(double a, double b) { return a / b; }
+    __device__ static __forceinline__ double shfl_xor(double a, int m) {
+        return __shfl_xor_sync(0xffffffffu, a, m);
+    }
+    __device__ static __forceinline__ double bcast0(double a) { return __shfl_sync(0xffffffffu, a, 0); }
+    __device__ static __forceinline__ double to_double(double a) { return a; }
+    __device__ static __forceinline__ double to_T(double a) { return a; }
+};
+
+template <typename T>
+__device__ __forceinline__ T fma_rn(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fma_rn<float>(float a, float b, float c) {
+    return __fmaf_rn(a, b, c);
+}
+template <>
+__device__ __forceinline__ double fma_rn<double>(double a, double b, double c) {
+    return __fma_rn(a, b, c);
+}
+
+// ---------------------------------------------------------------------------
+// Thread-block cluster primitives.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cluster_id_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t num_clusters_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+
+// Full cluster barrier: release orders this thread's earlier shared and
+// distributed-shared stores before the arrival, acquire makes the peers'
+// stores visible after the wait.  Every thread of every CTA takes part.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Address of the same shared-memory variable in CTA `rank` of this cluster.
+__device__ __forceinline__ uint32_t map_rank(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_cluster(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, dfloat v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.hi), "f"(v.lo)
+                 : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t addr, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier-completed distributed-shared-memory pushes.  st.async writes a
+// value into a peer CTA's shared memory and completes `bytes` of
+// transaction count on the peer's mbarrier; the receiver waits for the
+// phase, so no cluster-wide barrier or sender-side fence is needed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One local arrival that also raises the phase's expected transaction bytes.
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of `parity` with a deadline; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void st_async(uint32_t addr, float v, uint32_t mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+                 "r"(__float_as_uint(v)), "r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr),
+                 "l"(__double_as_longlong(v)), "r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t addr, dfloat v, uint32_t mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1, %2}, [%3];" ::"r"(
+                     addr),
+                 "r"(__float_as_uint(v.hi)), "r"(__float_as_uint(v.lo)), "r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_async_v4(uint32_t addr, float a, float b, float c, float d,
+                                            uint32_t mbar) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+        "r"(__float_as_uint(a)), "r"(__float_as_uint(b)), "r"(__float_as_uint(c)), "r"(__float_as_uint(d)),
+        "r"(mbar)
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Ragged batches: instance b owns knots [knot_off[b], knot_off[b+1]) and
+// controls [knot_off[b] - b, knot_off[b+1] - b - 1).  A single instance is
+// described by knot_off == nullptr and N1.
+// ---------------------------------------------------------------------------
+struct BatchView {
+    const int *knot_off;
+    int B;
+    int N1;
+    __device__ __forceinline__ void range(int b, int &k0, int &n) const {
+        if (knot_off) {
+            k0 = knot_off[b];
+            n = knot_off[b + 1] - k0;
+        } else {
+            k0 = 0;
+            n = N1;
+        }
+    }
+    // total knots of the batch
+    __device__ __forceinline__ int total() const { return knot_off ? knot_off[B] : N1; }
+    // instance that owns global knot kg (binary search over knot_off)
+    __device__ __forceinline__ int owner(int kg) const {
+        if (!knot_off) return 0;
+        int lo = 0, hi = B - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (knot_off[mid] <= kg) lo = mid; else hi = mid - 1;
+        }
+        return lo;
+    }
+};
+
+__host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace mpcg

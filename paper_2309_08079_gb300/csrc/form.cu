@@ -1,0 +1,434 @@
+// Per-knot kernels of the solve path: Schur complement and gamma
+// (Sec. II-B, Eq. trajoptSchur_1/2), the symmetric stair preconditioner
+// (Sec. IV-A), primal step recovery (Eq. schur), and the element-wise parts
+// of the backward pass.
+//
+// Every kernel assigns one group of G threads to one block row (knot) and
+// stages that knot's small blocks in shared memory; G = 32 (one warp) for
+// nx <= 16 and 128 otherwise.  Knots of a ragged batch are numbered
+// globally; a group finds its instance by binary search over knot_off.
+#include <type_traits>
+
+#include "launch.cuh"
+
+namespace mpcg {
+
+constexpr int FORM_THREADS = 128;
+
+__host__ __device__ __forceinline__ int group_size(int nx) { return nx <= 16 ? 32 : 128; }
+
+// Synchronise the threads of one group (a warp, or the whole CTA).
+__device__ __forceinline__ void group_sync(int G) {
+    if (G == 32) __syncwarp();
+    else __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ bool good_weight(T v) {
+    return v > T(0) && isfinite((double)v);
+}
+
+// ---------------------------------------------------------------------------
+// form_schur: block row k of S+ and gamma_k.
+//   k = 0: D_0 = Qd_0^-1, gamma_0 = c_0 - Qd_0^-1 q_0
+//   k > 0: D_k = theta_{k-1}, So[k-1] = phi_{k-1}, gamma_k = c_k - zeta_{k-1}
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FORM_THREADS) form_schur_kernel(const SchurArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = a.nx, nu = a.nu;
+    const int G = group_size(nx);
+    const int groups = FORM_THREADS / G;
+    const int g = threadIdx.x / G, t = threadIdx.x % G;
+    const int kg = blockIdx.x * groups + g;
+    // per-group scratch
+    const size_t per = (size_t)2 * nx * nx + 2 * nx * nu + 4 * nx + 2 * nu;
+    T *S = reinterpret_cast<T *>(smem_raw) + per * g;
+    T *Am = S, *As = Am + nx * nx, *Bm = As + nx * nx, *Bs = Bm + nx * nu;
+    T *iq0 = Bs + nx * nu, *iq1 = iq0 + nx, *qs = iq1 + nx, *q1 = qs + nx, *ir = q1 + nx,
+      *rs = ir + nu;
+    if (kg >= a.bv.total()) return;  // whole group leaves together
+    const int b = a.bv.owner(kg);
+    int k0, Nb;
+    a.bv.range(b, k0, Nb);
+    const int k = kg - k0;
+    bool bad = false;
+    const T *Qk = a.Qd + (size_t)kg * nx;
+    for (int i = t; i < nx; i += G) {
+        T v = Qk[i];
+        bad |= !good_weight(v);
+        iq1[i] = T(1) / v;
+        q1[i] = a.q[(size_t)kg * nx + i];
+    }
+    if (k == 0) {
+        group_sync(G);
+        T *Sd = a.Sd + (size_t)kg * nx * nx;
+        for (int e = t; e < nx * nx; e += G) {
+            int i = e / nx, j = e % nx;
+            Sd[e] = i == j ? iq1[i] : T(0);
+        }
+        for (int i = t; i < nx; i += G)
+            a.gamma[(size_t)kg * nx + i] = a.c[(size_t)kg * nx + i] - q1[i] * iq1[i];
+    } else {
+        const int j = kg - b - 1;  // control index of (A, B, Rd, r, So) for this row
+        const T *Ak = a.A + (size_t)j * nx * nx;
+        const T *Bk = a.B + (size_t)j * nx * nu;
+        for (int i = t; i < nx; i += G) {
+            T v = a.Qd[(size_t)(kg - 1) * nx + i];
+            bad |= !good_weight(v);
+            iq0[i] = T(1) / v;
+            qs[i] = a.q[(size_t)(kg - 1) * nx + i] / v;
+        }
+        for (int i = t; i < nu; i += G) {
+            T v = a.Rd[(size_t)j * nu + i];
+            bad |= !good_weight(v);
+            ir[i] = T(1) / v;
+            rs[i] = a.r[(size_t)j * nu + i] / v;
+        }
+        group_sync(G);
+        for (int e = t; e < nx * nx; e += G) {
+            T v = Ak[e];
+            Am[e] = v;
+            As[e] = v * iq0[e % nx];
+        }
+        for (int e = t; e < nx * nu; e += G) {
+            T v = Bk[e];
+            Bm[e] = v;
+            Bs[e] = v * ir[e % nu];
+        }
+        group_sync(G);
+        T *Sd = a.Sd + (size_t)kg * nx * nx;
+        T *So = a.So + (size_t)j * nx * nx;
+        // theta (upper triangle computed once, mirrored: exactly symmetric)
+        for (int e = t; e < nx * nx; e += G) {
+            const int i = e / nx, jj = e % nx;
+            So[e] = -As[e];
+            if (i > jj) continue;
+            T s = T(0);
+            for (int m = 0; m < nx; ++m) s += As[i * nx + m] * Am[jj * nx + m];
+            for (int m = 0; m < nu; ++m) s += Bs[i * nu + m] * Bm[jj * nu + m];
+            if (i == jj) s += iq1[i];
+            Sd[i * nx + jj] = s;
+            Sd[jj * nx + i] = s;
+        }
+        // zeta and gamma
+        for (int i = t; i < nx; i += G) {
+            T z = q1[i] * iq1[i];
+            for (int m = 0; m < nx; ++m) z -= Am[i * nx + m] * qs[m];
+            for (int m = 0; m < nu; ++m) z -= Bm[i * nu + m] * rs[m];
+            a.gamma[(size_t)kg * nx + i] = a.c[(size_t)kg * nx + i] - z;
+        }
+    }
+    if (a.info && __any_sync(0xffffffffu, bad) && (t % 32) == 0) atomicOr(&a.info[b], MPCG_INFO_BADINPUT);
+}
+
+// ---------------------------------------------------------------------------
+// form_precon, part 1: Pd[k] = Sd[k]^-1 by Gauss-Jordan elimination without
+// pivoting (Sd[k] is symmetric positive definite), symmetrised on output.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FORM_THREADS)
+precon_inv_kernel(int nx, BatchView bv, const T *__restrict__ Sd, T *__restrict__ Pd) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = group_size(nx);
+    const int groups = FORM_THREADS / G;
+    const int g = threadIdx.x / G, t = threadIdx.x % G;
+    const int kg = blockIdx.x * groups + g;
+    T *M = reinterpret_cast<T *>(smem_raw) + (size_t)g * nx * nx;
+    if (kg >= bv.total()) return;
+    const T *src = Sd + (size_t)kg * nx * nx;
+    for (int e = t; e < nx * nx; e += G) M[e] = src[e];
+    group_sync(G);
+    for (int j = 0; j < nx; ++j) {
+        const T d = T(1) / M[j * nx + j];
+        for (int c = t; c < nx; c += G)
+            if (c != j) M[j * nx + c] *= d;
+        group_sync(G);
+        const int n1 = nx - 1;
+        for (int e = t; e < n1 * n1; e += G) {
+            int i = e / n1, c = e % n1;
+            i += (i >= j);
+            c += (c >= j);
+            M[i * nx + c] -= M[i * nx + j] * M[j * nx + c];
+        }
+        group_sync(G);
+        for (int i = t; i < nx; i += G) {
+            if (i != j) M[i * nx + j] = -M[i * nx + j] * d;
+            else M[j * nx + j] = d;
+        }
+        group_sync(G);
+    }
+    T *dst = Pd + (size_t)kg * nx * nx;
+    for (int e = t; e < nx * nx; e += G) {
+        int i = e / nx, c = e % nx;
+        dst[e] = T(0.5) * (M[i * nx + c] + M[c * nx + i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// form_precon, part 2: Po[j] = -Pd[k+1] So[j] Pd[k] for every knot k that has
+// a successor in its instance (j = its control index).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FORM_THREADS)
+precon_off_kernel(int nx, BatchView bv, const T *__restrict__ Pd,
+                  const T *__restrict__ So, T *__restrict__ Po) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = group_size(nx);
+    const int groups = FORM_THREADS / G;
+    const int g = threadIdx.x / G, t = threadIdx.x % G;
+    const int kg = blockIdx.x * groups + g;
+    const int n2 = nx * nx;
+    T *X = reinterpret_cast<T *>(smem_raw) + (size_t)g * 4 * n2;
+    T *S = X + n2, *Y = S + n2, *T1 = Y + n2;
+    if (kg >= bv.total()) return;
+    const int b = bv.owner(kg);
+    int k0, Nb;
+    bv.range(b, k0, Nb);
+    if (kg - k0 + 1 >= Nb) return;  // last knot of its instance
+    const int j = kg - b;
+    for (int e = t; e < n2; e += G) {
+        X[e] = Pd[(size_t)kg * n2 + e];
+        Y[e] = Pd[(size_t)(kg + 1) * n2 + e];
+        S[e] = So[(size_t)j * n2 + e];
+    }
+    group_sync(G);
+    for (int e = t; e < n2; e += G) {
+        int i = e / nx, c = e % nx;
+        T s = T(0);
+        for (int m = 0; m < nx; ++m) s += S[i * nx + m] * X[m * nx + c];
+        T1[e] = s;
+    }
+    group_sync(G);
+    for (int e = t; e < n2; e += G) {
+        int i = e / nx, c = e % nx;
+        T s = T(0);
+        for (int m = 0; m < nx; ++m) s += Y[i * nx + m] * T1[m * nx + c];
+        Po[(size_t)j * n2 + e] = -s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// recover: z = G^-1 (C^T v - h) for a multiplier-shaped v and h = (hx, hu):
+//   zx_k = (v_k - A_k^T v_{k+1} - hx_k) / Qd_k   (last knot: no A term)
+//   zu_k = (-B_k^T v_{k+1} - hu_k) / Rd_k
+// With (v, h) = (lambda, g) this is dz (Eq. schur); with (mu, dL/ddz) it is
+// the adjoint's g_bar.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FORM_THREADS)
+recover_kernel(int nx, int nu, BatchView bv, const T *__restrict__ A,
+               const T *__restrict__ B, const T *__restrict__ Qd, const T *__restrict__ Rd,
+               const T *__restrict__ hx, const T *__restrict__ hu, const T *__restrict__ v,
+               T *__restrict__ zx, T *__restrict__ zu) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = group_size(nx);
+    const int groups = FORM_THREADS / G;
+    const int g = threadIdx.x / G, t = threadIdx.x % G;
+    const int kg = blockIdx.x * groups + g;
+    T *vn = reinterpret_cast<T *>(smem_raw) + (size_t)g * nx;
+    if (kg >= bv.total()) return;
+    const int b = bv.owner(kg);
+    int k0, Nb;
+    bv.range(b, k0, Nb);
+    const bool last = kg - k0 + 1 >= Nb;
+    const int j = kg - b;
+    for (int i = t; i < nx; i += G) vn[i] = last ? T(0) : v[(size_t)(kg + 1) * nx + i];
+    group_sync(G);
+    for (int i = t; i < nx + nu; i += G) {
+        if (i < nx) {
+            T s = v[(size_t)kg * nx + i] - hx[(size_t)kg * nx + i];
+            if (!last) {
+                const T *Ak = A + (size_t)j * nx * nx;
+                for (int m = 0; m < nx; ++m) s -= Ak[m * nx + i] * vn[m];
+            }
+            zx[(size_t)kg * nx + i] = s / Qd[(size_t)kg * nx + i];
+        } else if (!last) {
+            const int u = i - nx;
+            const T *Bk = B + (size_t)j * nx * nu;
+            T s = -hu[(size_t)j * nu + u];
+            for (int m = 0; m < nx; ++m) s -= Bk[m * nu + u] * vn[m];
+            zu[(size_t)j * nu + u] = s / Rd[(size_t)j * nu + u];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward seed: out = w + C G^-1 (hx, hu), block row k:
+//   k = 0: w_0 + hx_0 / Qd_0
+//   k > 0: w_k - A_{k-1} (hx_{k-1}/Qd_{k-1}) - B_{k-1} (hu_{k-1}/Rd_{k-1}) + hx_k/Qd_k
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FORM_THREADS)
+cgh_kernel(int nx, int nu, BatchView bv, const T *__restrict__ A,
+           const T *__restrict__ B, const T *__restrict__ Qd, const T *__restrict__ Rd,
+           const T *__restrict__ hx, const T *__restrict__ hu, const T *__restrict__ w,
+           T *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = group_size(nx);
+    const int groups = FORM_THREADS / G;
+    const int g = threadIdx.x / G, t = threadIdx.x % G;
+    const int kg = blockIdx.x * groups + g;
+    T *xs = reinterpret_cast<T *>(smem_raw) + (size_t)g * (nx + nu);
+    T *us = xs + nx;
+    if (kg >= bv.total()) return;
+    const int b = bv.owner(kg);
+    int k0, Nb;
+    bv.range(b, k0, Nb);
+    const int k = kg - k0;
+    const int j = kg - b - 1;
+    if (k > 0) {
+        for (int i = t; i < nx; i += G) xs[i] = hx[(size_t)(kg - 1) * nx + i] / Qd[(size_t)(kg - 1) * nx + i];
+        for (int i = t; i < nu; i += G) us[i] = hu[(size_t)j * nu + i] / Rd[(size_t)j * nu + i];
+    }
+    group_sync(G);
+    for (int i = t; i < nx; i += G) {
+        T s = w[(size_t)kg * nx + i] + hx[(size_t)kg * nx + i] / Qd[(size_t)kg * nx + i];
+        if (k > 0) {
+            const T *Ak = A + (size_t)j * nx * nx;
+            const T *Bk = B + (size_t)j * nx * nu;
+            for (int m = 0; m < nx; ++m) s -= Ak[i * nx + m] * xs[m];
+            for (int m = 0; m < nu; ++m) s -= Bk[i * nu + m] * us[m];
+        }
+        out[(size_t)kg * nx + i] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Backward outer products (gq = g_bar_x and gr = g_bar_u already written):
+//   Qd_bar = g_bar_x * dx, Rd_bar = g_bar_u * du, c_bar = -mu,
+//   A_bar_k = mu_{k+1} dx_k^T + lam_{k+1} g_bar_x_k^T,
+//   B_bar_k = mu_{k+1} du_k^T + lam_{k+1} g_bar_u_k^T.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FORM_THREADS)
+grad_kernel(int nx, int nu, BatchView bv, const T *__restrict__ lam,
+            const T *__restrict__ mu, const T *__restrict__ dx, const T *__restrict__ du,
+            const T *__restrict__ gq, const T *__restrict__ gr, T *__restrict__ gA,
+            T *__restrict__ gB, T *__restrict__ gQd, T *__restrict__ gRd, T *__restrict__ gc) {
+    const int G = group_size(nx);
+    const int groups = FORM_THREADS / G;
+    const int g = threadIdx.x / G, t = threadIdx.x % G;
+    const int kg = blockIdx.x * groups + g;
+    if (kg >= bv.total()) return;
+    const int b = bv.owner(kg);
+    int k0, Nb;
+    bv.range(b, k0, Nb);
+    const bool last = kg - k0 + 1 >= Nb;
+    const int j = kg - b;
+    for (int i = t; i < nx; i += G) {
+        const size_t o = (size_t)kg * nx + i;
+        gQd[o] = gq[o] * dx[o];
+        gc[o] = -mu[o];
+    }
+    if (last) return;
+    for (int i = t; i < nu; i += G) {
+        const size_t o = (size_t)j * nu + i;
+        gRd[o] = gr[o] * du[o];
+    }
+    const T *mun = mu + (size_t)(kg + 1) * nx, *lamn = lam + (size_t)(kg + 1) * nx;
+    for (int e = t; e < nx * nx; e += G) {
+        int i = e / nx, m = e % nx;
+        gA[(size_t)j * nx * nx + e] = mun[i] * dx[(size_t)kg * nx + m] + lamn[i] * gq[(size_t)kg * nx + m];
+    }
+    for (int e = t; e < nx * nu; e += G) {
+        int i = e / nu, m = e % nu;
+        gB[(size_t)j * nx * nu + e] = mun[i] * du[(size_t)j * nu + m] + lamn[i] * gr[(size_t)j * nu + m];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+static inline int form_grid(int nx, int Ktot) {
+    const int groups = FORM_THREADS / group_size(nx);
+    return ceil_div(Ktot, groups);
+}
+
+template <typename T>
+cudaError_t launch_form_schur(const SchurArgs<T> &a, cudaStream_t s) {
+    const int G = group_size(a.nx);
+    const size_t per = (size_t)2 * a.nx * a.nx + 2 * a.nx * a.nu + 4 * a.nx + 2 * a.nu;
+    const size_t smem = per * sizeof(T) * (FORM_THREADS / G);
+    form_schur_kernel<T><<<form_grid(a.nx, a.Kgrid), FORM_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_form_precon(int nx, BatchView bv, int Kgrid, const T *Sd, const T *So, T *Pd,
+                               T *Po, cudaStream_t s) {
+    const int groups = FORM_THREADS / group_size(nx);
+    size_t smem1 = sizeof(T) * (size_t)nx * nx * groups;
+    size_t smem2 = sizeof(T) * (size_t)4 * nx * nx * groups;
+    cudaError_t e;
+    precon_inv_kernel<T><<<form_grid(nx, Kgrid), FORM_THREADS, smem1, s>>>(nx, bv, Sd, Pd);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    precon_off_kernel<T><<<form_grid(nx, Kgrid), FORM_THREADS, smem2, s>>>(nx, bv, Pd, So, Po);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_recover(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B,
+                           const T *Qd, const T *Rd, const T *hx, const T *hu, const T *v, T *zx,
+                           T *zu, cudaStream_t s) {
+    const int groups = FORM_THREADS / group_size(nx);
+    recover_kernel<T><<<form_grid(nx, Kgrid), FORM_THREADS, sizeof(T) * nx * groups, s>>>(
+        nx, nu, bv, A, B, Qd, Rd, hx, hu, v, zx, zu);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cgh(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B,
+                       const T *Qd, const T *Rd, const T *hx, const T *hu, const T *w, T *out,
+                       cudaStream_t s) {
+    const int groups = FORM_THREADS / group_size(nx);
+    cgh_kernel<T><<<form_grid(nx, Kgrid), FORM_THREADS, sizeof(T) * (nx + nu) * groups, s>>>(
+        nx, nu, bv, A, B, Qd, Rd, hx, hu, w, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_grad(int nx, int nu, BatchView bv, int Kgrid, const T *lam, const T *mu,
+                        const T *dx, const T *du, const T *gq, const T *gr, T *gA, T *gB, T *gQd,
+                        T *gRd, T *gc, cudaStream_t s) {
+    grad_kernel<T><<<form_grid(nx, Kgrid), FORM_THREADS, 0, s>>>(nx, nu, bv, lam, mu, dx, du,
+                                                                  gq, gr, gA, gB, gQd, gRd, gc);
+    return cudaGetLastError();
+}
+
+// Raise every per-knot kernel's dynamic shared-memory ceiling once per device
+// (large nx needs more than the 48 KB default).
+template <typename T>
+static cudaError_t form_prepare_t(int smem_optin) {
+    cudaError_t e;
+    const auto a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if ((e = cudaFuncSetAttribute(form_schur_kernel<T>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(precon_inv_kernel<T>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(precon_off_kernel<T>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(recover_kernel<T>, a, smem_optin))) return e;
+    return cudaFuncSetAttribute(cgh_kernel<T>, a, smem_optin);
+}
+
+cudaError_t form_prepare(int smem_optin) {
+    cudaError_t e = form_prepare_t<float>(smem_optin);
+    return e != cudaSuccess ? e : form_prepare_t<double>(smem_optin);
+}
+
+#define MPCG_INST(T)                                                                              \
+    template cudaError_t launch_form_schur<T>(const SchurArgs<T> &, cudaStream_t);                \
+    template cudaError_t launch_form_precon<T>(int, BatchView, int, const T *, const T *, T *,    \
+                                               T *, cudaStream_t);                                \
+    template cudaError_t launch_recover<T>(int, int, BatchView, int, const T *, const T *,        \
+                                           const T *, const T *, const T *, const T *, const T *, \
+                                           T *, T *, cudaStream_t);                               \
+    template cudaError_t launch_cgh<T>(int, int, BatchView, int, const T *, const T *, const T *, \
+                                       const T *, const T *, const T *, const T *, T *,           \
+                                       cudaStream_t);                                             \
+    template cudaError_t launch_grad<T>(int, int, BatchView, int, const T *, const T *,           \
+                                        const T *, const T *, const T *, const T *, T *, T *,     \
+                                        T *, T *, T *, cudaStream_t);
+MPCG_INST(float)
+MPCG_INST(double)
+#undef MPCG_INST
+
+}  // namespace mpcg

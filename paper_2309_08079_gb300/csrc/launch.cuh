@@ -1,0 +1,69 @@
+// Internal launch interface shared by api.cu, form.cu and pcg.cu.
+#pragma once
+
+#include "common.cuh"
+
+namespace mpcg {
+
+template <typename T>
+struct SchurArgs {
+    int nx, nu;
+    BatchView bv;
+    int Kgrid;  // host-side upper bound on the total knots (grid size only)
+    const T *A, *B, *Qd, *Rd, *q, *r, *c;
+    T *Sd, *So, *gamma;
+    unsigned *info;
+};
+
+enum { MODE_REG = 0, MODE_PTR = 1 };
+
+template <typename T>
+struct PcgParams {
+    int nx;
+    BatchView bv;
+    const T *Sd, *So, *Pd, *Po;
+    const T *rhs;  // b = rhs_sign * rhs
+    T rhs_sign;
+    T *lam;
+    const unsigned *info;
+    mpcg_stats *stats;
+    int *queue;       // instance counter (nullptr: static round robin)
+    double tol;
+    int tol_mode;
+    int max_iter;     // <= 0: 10 N nx
+    int kpc_max;      // knot slots per CTA (blockDim.x / LPK)
+    int stage_smem;   // PTR mode: stage blocks in shared memory
+    int vs;           // shared vector stride (elements per knot)
+};
+
+struct PcgLaunch {
+    int C;         // CTAs per cluster
+    int clusters;  // clusters in the grid
+    int threads;   // threads per CTA
+    int lpk, rpt, mode, stage, vs, kpc_max;
+    size_t smem;
+};
+
+template <typename T> cudaError_t launch_form_schur(const SchurArgs<T> &, cudaStream_t);
+template <typename T>
+cudaError_t launch_form_precon(int nx, BatchView bv, int Kgrid, const T *Sd, const T *So, T *Pd,
+                               T *Po, cudaStream_t s);
+template <typename T>
+cudaError_t launch_recover(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B,
+                           const T *Qd, const T *Rd, const T *hx, const T *hu, const T *v, T *zx,
+                           T *zu, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cgh(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B,
+                       const T *Qd, const T *Rd, const T *hx, const T *hu, const T *w, T *out,
+                       cudaStream_t s);
+template <typename T>
+cudaError_t launch_grad(int nx, int nu, BatchView bv, int Kgrid, const T *lam, const T *mu,
+                        const T *dx, const T *du, const T *gq, const T *gr, T *gA, T *gB, T *gQd,
+                        T *gRd, T *gc, cudaStream_t s);
+template <typename T> cudaError_t pcg_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
+template <typename T> int pcg_max_clusters(const PcgLaunch &);
+cudaError_t pcg_prepare(int smem_optin);
+cudaError_t form_prepare(int smem_optin);
+template <typename T> size_t pcg_smem_bytes(int kpc_max, int vs, int C, int W, int nx, int stage);
+
+}  // namespace mpcg

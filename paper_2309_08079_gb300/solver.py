@@ -1,0 +1,243 @@
+"""PyTorch-facing binding of libmpcg.so.
+
+PyTorch supplies device memory and the current stream; every step of the
+solve path runs in the library's CUDA kernels.  Functions keep the C names
+of the entry points they call (form_schur, form_precon, pcg_solve,
+recover_step, backward) and only marshal tensor pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_DT = {torch.float32: 0, torch.float64: 1}
+STATS_DTYPE = np.dtype([("iters", "<i4"), ("status", "<i4"), ("eta", "<f8"), ("relres", "<f8")])
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class LQTensors:
+    """LQ data on the device (layouts of include/mpcg.h).
+
+    For a ragged batch, knot_off is an int32 device tensor of B+1 offsets and
+    N is the largest horizon; for a single instance knot_off is None.
+    """
+    nx: int
+    nu: int
+    N: int
+    A: torch.Tensor
+    B: torch.Tensor
+    Qd: torch.Tensor
+    Rd: torch.Tensor
+    q: torch.Tensor
+    r: torch.Tensor
+    c: torch.Tensor
+    knot_off: Optional[torch.Tensor] = None
+    nb: int = 1            # number of instances
+    total: int = 0         # total knots
+
+    FIELDS = ("A", "B", "Qd", "Rd", "q", "r", "c")
+
+    @property
+    def dtype(self):
+        return self.A.dtype
+
+    @property
+    def device(self):
+        return self.A.device
+
+    @property
+    def batched(self) -> bool:
+        return self.knot_off is not None
+
+    def dims(self) -> L.mpcg_dims:
+        return L.mpcg_dims(self.nx, self.nu, self.N, _DT[self.dtype])
+
+    def lq_struct(self) -> L.mpcg_lq:
+        return L.mpcg_lq(*(t.data_ptr() for t in (self.A, self.B, self.Qd, self.Rd, self.q,
+                                                   self.r, self.c)))
+
+    @staticmethod
+    def from_numpy(lq, device="cuda", dtype=torch.float32) -> "LQTensors":
+        t = {f: torch.as_tensor(np.ascontiguousarray(getattr(lq, f)), dtype=dtype, device=device)
+             for f in LQTensors.FIELDS}
+        return LQTensors(lq.nx, lq.nu, lq.N, **t, knot_off=None, nb=1, total=lq.N)
+
+    @staticmethod
+    def from_batch(batch, device="cuda", dtype=torch.float32) -> "LQTensors":
+        t = {f: torch.as_tensor(np.ascontiguousarray(getattr(batch.lq, f)), dtype=dtype,
+                                device=device) for f in LQTensors.FIELDS}
+        ko = torch.as_tensor(batch.knot_off.astype(np.int32), device=device)
+        return LQTensors(batch.nx, batch.nu, int(batch.Ns.max()), **t, knot_off=ko,
+                         nb=batch.B, total=int(batch.knot_off[-1]))
+
+
+@dataclass
+class SchurTensors:
+    Sd: torch.Tensor
+    So: torch.Tensor
+    Pd: torch.Tensor
+    Po: torch.Tensor
+    gamma: torch.Tensor
+    info: torch.Tensor
+
+    def struct(self) -> L.mpcg_schur:
+        return L.mpcg_schur(*(t.data_ptr() for t in (self.Sd, self.So, self.Pd, self.Po,
+                                                      self.gamma, self.info)))
+
+
+def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0) -> L.mpcg_opts:
+    return L.mpcg_opts(float(tol), int(tol_mode), int(max_iter), int(cluster), 0)
+
+
+def read_stats(stats: torch.Tensor) -> np.ndarray:
+    """Device stats buffer -> numpy structured array (iters, status, eta, relres)."""
+    return stats.cpu().numpy().view(STATS_DTYPE)
+
+
+class Solver:
+    """Owns one library handle bound to a CUDA device."""
+
+    def __init__(self, device=None):
+        self.lib = L.load()
+        self.device = torch.device(device if device is not None else "cuda")
+        with torch.cuda.device(self.device):
+            h = C.c_void_p()
+            L.check("mpcg_create", self.lib.mpcg_create(C.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) and self.h.value:
+                self.lib.mpcg_destroy(self.h)
+                self.h = C.c_void_p()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- buffers
+    def alloc_schur(self, lq: LQTensors) -> SchurTensors:
+        nx, K, dt, dev = lq.nx, lq.total, lq.dtype, lq.device
+        Kc = K - lq.nb
+        e = lambda *s: torch.empty(*s, dtype=dt, device=dev)
+        return SchurTensors(e(K, nx, nx), e(max(Kc, 1), nx, nx), e(K, nx, nx),
+                            e(max(Kc, 1), nx, nx), e(K, nx),
+                            torch.zeros(lq.nb, dtype=torch.int32, device=dev))
+
+    def alloc_stats(self, nb: int = 1, device=None) -> torch.Tensor:
+        return torch.zeros(nb * L.STATS_BYTES, dtype=torch.uint8,
+                           device=device if device is not None else self.device)
+
+    def workspace_bytes(self, lq: LQTensors) -> int:
+        return int(self.lib.mpcg_workspace_bytes(lq.dims(), lq.nb))
+
+    def alloc_workspace(self, lq: LQTensors) -> torch.Tensor:
+        return torch.zeros(self.workspace_bytes(lq), dtype=torch.uint8, device=lq.device)
+
+    # ---------------------------------------------------------------- the path
+    def form_schur(self, lq: LQTensors, schur: SchurTensors, stream=None) -> SchurTensors:
+        ls, ss = lq.lq_struct(), schur.struct()
+        if lq.batched:
+            rc = self.lib.mpcg_form_schur_batched(self.h, lq.dims(), lq.nb, _ptr(lq.knot_off),
+                                                  C.byref(ls), C.byref(ss), _stream(stream))
+        else:
+            rc = self.lib.mpcg_form_schur(self.h, lq.dims(), C.byref(ls), C.byref(ss),
+                                          _stream(stream))
+        L.check("mpcg_form_schur", rc)
+        return schur
+
+    def form_precon(self, lq: LQTensors, schur: SchurTensors, stream=None) -> SchurTensors:
+        ss = schur.struct()
+        if lq.batched:
+            rc = self.lib.mpcg_form_precon_batched(self.h, lq.dims(), lq.nb, _ptr(lq.knot_off),
+                                                   C.byref(ss), _stream(stream))
+        else:
+            rc = self.lib.mpcg_form_precon(self.h, lq.dims(), C.byref(ss), _stream(stream))
+        L.check("mpcg_form_precon", rc)
+        return schur
+
+    def pcg_solve(self, lq: LQTensors, schur: SchurTensors, lam: torch.Tensor, opts=None,
+                  stats: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+        """Solve S+ lam = -gamma in place (lam holds the warm start)."""
+        ss = schur.struct()
+        o = opts if opts is not None else make_opts()
+        if stats is None:
+            stats = self.alloc_stats(lq.nb, lq.device)
+        if lq.batched:
+            if workspace is None:
+                workspace = self.alloc_workspace(lq)
+            rc = self.lib.mpcg_pcg_solve_batched(self.h, lq.dims(), lq.nb, _ptr(lq.knot_off),
+                                                 C.byref(ss), _ptr(lam), C.byref(o), _ptr(stats),
+                                                 _ptr(workspace), _stream(stream))
+        else:
+            rc = self.lib.mpcg_pcg_solve(self.h, lq.dims(), C.byref(ss), _ptr(lam), C.byref(o),
+                                         _ptr(stats), _stream(stream))
+        L.check("mpcg_pcg_solve", rc)
+        return stats
+
+    def recover_step(self, lq: LQTensors, lam: torch.Tensor, dx=None, du=None, stream=None):
+        if dx is None:
+            dx = torch.empty(lq.total, lq.nx, dtype=lq.dtype, device=lq.device)
+        if du is None:
+            du = torch.empty(max(lq.total - lq.nb, 1), lq.nu, dtype=lq.dtype, device=lq.device)
+        ls = lq.lq_struct()
+        if lq.batched:
+            rc = self.lib.mpcg_recover_step_batched(self.h, lq.dims(), lq.nb, _ptr(lq.knot_off),
+                                                    C.byref(ls), _ptr(lam), _ptr(dx), _ptr(du),
+                                                    _stream(stream))
+        else:
+            rc = self.lib.mpcg_recover_step(self.h, lq.dims(), C.byref(ls), _ptr(lam), _ptr(dx),
+                                            _ptr(du), _stream(stream))
+        L.check("mpcg_recover_step", rc)
+        return dx, du
+
+    def solve(self, lq: LQTensors, lam0: Optional[torch.Tensor] = None, opts=None,
+              schur: Optional[SchurTensors] = None, stats=None, workspace=None, stream=None):
+        """The whole path: form_schur, form_precon, pcg_solve, recover_step.
+
+        Returns (lam, dx, du, stats, schur); lam0 (if given) is overwritten.
+        """
+        if schur is None:
+            schur = self.alloc_schur(lq)
+        lam = lam0 if lam0 is not None else torch.zeros(lq.total, lq.nx, dtype=lq.dtype,
+                                                        device=lq.device)
+        self.form_schur(lq, schur, stream)
+        self.form_precon(lq, schur, stream)
+        stats = self.pcg_solve(lq, schur, lam, opts, stats, workspace, stream)
+        dx, du = self.recover_step(lq, lam, stream=stream)
+        return lam, dx, du, stats, schur
+
+    def backward(self, lq: LQTensors, schur: SchurTensors, lam, dx, du, lam_bar, dx_bar, du_bar,
+                 opts=None, stats=None, workspace=None, stream=None):
+        """Gradients of a loss of (lam, dx, du) w.r.t. (A, B, Qd, Rd, q, r, c)."""
+        g = {f: torch.empty_like(getattr(lq, f)) for f in LQTensors.FIELDS}
+        gs = L.mpcg_grads(*(g[f].data_ptr() for f in LQTensors.FIELDS))
+        o = opts if opts is not None else make_opts()
+        if stats is None:
+            stats = self.alloc_stats(lq.nb, lq.device)
+        if workspace is None:
+            workspace = self.alloc_workspace(lq)
+        ls, ss = lq.lq_struct(), schur.struct()
+        args = (C.byref(ls), C.byref(ss), _ptr(lam), _ptr(dx), _ptr(du), _ptr(lam_bar),
+                _ptr(dx_bar), _ptr(du_bar), C.byref(gs), C.byref(o), _ptr(stats),
+                _ptr(workspace), _stream(stream))
+        if lq.batched:
+            rc = self.lib.mpcg_backward_batched(self.h, lq.dims(), lq.nb, _ptr(lq.knot_off), *args)
+        else:
+            rc = self.lib.mpcg_backward(self.h, lq.dims(), *args)
+        L.check("mpcg_backward", rc)
+        return g, stats

@@ -1,0 +1,93 @@
+"""Batched (ragged-horizon) solves against the oracle, instance by instance."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import TOL_F32, TOL_F64, solver
+from workload import gen
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_batch(batch, dtype="float32", lam0=None, opts=None):
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors, read_stats
+    tdt = torch.float32 if dtype == "float32" else torch.float64
+    s = solver()
+    lt = LQTensors.from_batch(batch, dtype=tdt)
+    lam = None if lam0 is None else torch.as_tensor(lam0, dtype=tdt, device="cuda").clone()
+    lam, dx, du, stats, _ = s.solve(lt, lam, opts=opts)
+    torch.cuda.synchronize()
+    return (lam.cpu().double().numpy(), dx.cpu().double().numpy(), du.cpu().double().numpy(),
+            read_stats(stats))
+
+
+def _check(batch, lam, dx, du, st, tol):
+    ko = batch.knot_off
+    co = batch.ctrl_off()
+    for b, it in enumerate(batch.items):
+        lo, xo, uo = oracle.kkt_solve(it.astype(np.float64))
+        assert st["status"][b] == 0, (b, st[b])
+        e_lam = oracle.relerr(lam[ko[b]:ko[b + 1]], lo)
+        z = np.concatenate([dx[ko[b]:ko[b + 1]].ravel(), du[co[b]:co[b + 1]].ravel()])
+        e_dz = oracle.relerr(z, np.concatenate([xo.ravel(), uo.ravel()]))
+        assert e_lam < tol and e_dz < tol, (b, it.N, e_lam, e_dz)
+
+
+@pytest.mark.parametrize("Ns", [[1, 5, 32, 33, 100, 64], [512, 3, 257], [2] * 7])
+def test_batched_ragged_parity(Ns):
+    batch = gen.kuka_batch(14, 7, Ns, 1000).astype(np.float32)
+    lam, dx, du, st = _run_batch(batch)
+    _check(batch, lam, dx, du, st, TOL_F32)
+
+
+def test_batched_queue_more_instances_than_clusters():
+    Ns = gen.batch_horizons(300, 8, 64, 3)
+    batch = gen.kuka_batch(14, 7, Ns, 2000).astype(np.float32)
+    lam, dx, du, st = _run_batch(batch)
+    _check(batch, lam, dx, du, st, TOL_F32)
+
+
+def test_batched_other_shapes_and_f64():
+    from paper_2309_08079_gb300.solver import make_opts
+    batch = gen.kuka_batch(4, 2, [3, 17, 40], 77)
+    lam, dx, du, st = _run_batch(batch, "float64", opts=make_opts(tol=1e-13))
+    _check(batch, lam, dx, du, st, TOL_F64)
+    batch36 = gen.kuka_batch(36, 12, [4, 16, 9], 78).astype(np.float32)
+    lam, dx, du, st = _run_batch(batch36)
+    _check(batch36, lam, dx, du, st, TOL_F32)
+
+
+def test_batched_matches_single_solves():
+    """A batch gives each instance what a single-instance call gives it."""
+    from gpu_util import run_gpu
+    Ns = [40, 7, 129]
+    batch = gen.kuka_batch(14, 7, Ns, 55).astype(np.float32)
+    lam, dx, du, st = _run_batch(batch)
+    ko = batch.knot_off
+    for b, it in enumerate(batch.items):
+        l1, _, _, s1, _ = run_gpu(it)
+        np.testing.assert_array_equal(lam[ko[b]:ko[b + 1]], l1)
+        assert s1["iters"][0] == st["iters"][b]
+
+
+def test_batched_poisoned_instance_isolated():
+    Ns = [20, 30, 25]
+    items = [gen.kuka_lq(14, 7, n, 900 + i) for i, n in enumerate(Ns)]
+    items[1].Rd[3, 0] = 0.0
+    batch = gen.concat_batch(items).astype(np.float32)
+    lam, dx, du, st = _run_batch(batch)
+    assert st["status"][1] == 4
+    for b in (0, 2):
+        assert st["status"][b] == 0
+        lo, _, _ = oracle.kkt_solve(batch.items[b].astype(np.float64))
+        assert oracle.relerr(lam[batch.knot_off[b]:batch.knot_off[b + 1]], lo) < TOL_F32
+
+
+def test_batched_warm_start():
+    Ns = [64, 200, 33]
+    batch = gen.kuka_batch(14, 7, Ns, 1500).astype(np.float32)
+    los = [oracle.kkt_solve(it.astype(np.float64))[0] for it in batch.items]
+    lam0 = np.concatenate([gen.warm_start(l, 1500 + i, 0) for i, l in enumerate(los)])
+    lam, dx, du, st = _run_batch(batch, lam0=lam0)
+    _check(batch, lam, dx, du, st, TOL_F32)

@@ -1,0 +1,170 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import TOL_F32, TOL_F64, parity, run_gpu, solver
+from workload import gen
+
+pytestmark = pytest.mark.gpu
+
+
+# ------------------------------------------------------------------ per-step
+def _schur_gpu(lq32):
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors
+    s = solver()
+    lt = LQTensors.from_numpy(lq32)
+    sch = s.alloc_schur(lt)
+    s.form_schur(lt, sch)
+    s.form_precon(lt, sch)
+    torch.cuda.synchronize()
+    return {k: getattr(sch, k).cpu().double().numpy() for k in ("Sd", "So", "Pd", "Po", "gamma")}
+
+
+@pytest.mark.parametrize("nx,nu,N", [(14, 7, 32), (14, 7, 45), (4, 2, 9), (36, 12, 6), (2, 1, 1)])
+def test_form_schur_and_precon(nx, nu, N):
+    lq32 = gen.kuka_lq(nx, nu, N, 100 + N).astype(np.float32)
+    g = _schur_gpu(lq32)
+    Sd, So, gamma = oracle.schur_blocks(lq32.astype(np.float64))
+    assert oracle.relerr(g["Sd"], Sd) < 1e-6
+    assert oracle.relerr(g["gamma"], gamma) < 1e-6
+    if N > 1:
+        assert oracle.relerr(g["So"][:N - 1], So) < 1e-6
+    Pd, Po = oracle.precon_blocks(Sd, So)
+    assert oracle.relerr(g["Pd"], Pd) < 1e-4
+    # Phi^-1 diagonal blocks are symmetric
+    assert np.abs(g["Pd"] - g["Pd"].transpose(0, 2, 1)).max() <= 1e-6 * np.abs(g["Pd"]).max()
+    if N > 1:
+        assert oracle.relerr(g["Po"][:N - 1], Po) < 1e-4
+
+
+# ------------------------------------------------------------------ single solves
+@pytest.mark.parametrize("N", [1, 2, 3, 32, 33, 47, 64, 100, 128, 256, 511, 512])
+def test_solve_parity_kuka_f32(N):
+    lq = gen.kuka_lq(14, 7, N, 2 + N)
+    e_lam, e_dz, st = parity(lq)
+    assert st["status"][0] == 0, st
+    assert e_lam < TOL_F32 and e_dz < TOL_F32, (e_lam, e_dz, st)
+
+
+def test_solve_config_small():
+    c = gen.CONFIG_SMALL
+    lq = gen.kuka_lq(c["nx"], c["nu"], c["N"], c["seed"], dt=c["dt"], qd=c["qd"])
+    e_lam, e_dz, st = parity(lq)
+    assert st["status"][0] == 0 and st["relres"][0] <= 1.01e-6
+    assert e_lam < TOL_F32 and e_dz < TOL_F32, (e_lam, e_dz)
+
+
+@pytest.mark.parametrize("nx,nu,N", [(2, 1, 5), (4, 2, 40), (6, 3, 17), (16, 8, 64), (20, 10, 24),
+                                     (36, 12, 16)])
+def test_solve_parity_other_shapes(nx, nu, N):
+    lq = gen.kuka_lq(nx, nu, N, 7 * N + nx)
+    e_lam, e_dz, st = parity(lq)
+    assert st["status"][0] == 0, st
+    assert e_lam < TOL_F32 and e_dz < TOL_F32, (e_lam, e_dz)
+
+
+@pytest.mark.parametrize("nx,nu,N", [(14, 7, 32), (14, 7, 512), (4, 2, 33), (36, 12, 20)])
+def test_solve_parity_f64(nx, nu, N):
+    from paper_2309_08079_gb300.solver import make_opts
+    lq = gen.kuka_lq(nx, nu, N, 300 + N)
+    e_lam, e_dz, st = parity(lq, dtype="float64", opts=make_opts(tol=1e-13))
+    assert st["status"][0] == 0, st
+    assert e_lam < TOL_F64 and e_dz < TOL_F64, (e_lam, e_dz)
+
+
+@pytest.mark.parametrize("C", [2, 3, 4, 8, 16])
+def test_cluster_sizes_agree(C):
+    from paper_2309_08079_gb300.solver import make_opts
+    lq = gen.kuka_lq(14, 7, 64, 5)
+    e_lam, e_dz, st = parity(lq, opts=make_opts(cluster=C))
+    assert st["status"][0] == 0 and e_lam < TOL_F32 and e_dz < TOL_F32
+
+
+def test_cluster_too_small_is_rejected():
+    """64 knots need at least 2 CTAs of 32 knot slots: C = 1 is refused
+    before any launch, and the next call still works."""
+    from paper_2309_08079_gb300._lib import MPCG_EUNSUPPORTED, MPCGError
+    from paper_2309_08079_gb300.solver import make_opts
+    lq = gen.kuka_lq(14, 7, 64, 5)
+    with pytest.raises(MPCGError) as ei:
+        parity(lq, opts=make_opts(cluster=1))
+    assert ei.value.code == MPCG_EUNSUPPORTED
+    e_lam, _, st = parity(lq)
+    assert st["status"][0] == 0 and e_lam < TOL_F32
+
+
+@pytest.mark.parametrize("N,rep", [(128, 0), (200, 1), (512, 2)])
+def test_warm_start_parity(N, rep):
+    """Warm start lambda* (1 + 0.01 xi): the noise touches every eigen-
+    component, so it saves no iterations against a 1e-6 relative test, but
+    the result must still meet the parity bar (the initial residual of a
+    warm start is formed in extended precision)."""
+    lq = gen.kuka_lq(14, 7, N, 130 + N)
+    lq32 = lq.astype(np.float32)
+    lo, _, _ = oracle.kkt_solve(lq32.astype(np.float64))
+    lam0 = gen.warm_start(lo, 130 + N, rep)
+    e_lam, e_dz, st = parity(lq, lam0=lam0)
+    assert st["status"][0] == 0 and e_lam < TOL_F32 and e_dz < TOL_F32, (e_lam, e_dz)
+
+
+def test_close_warm_start_takes_fewer_iterations():
+    lq = gen.kuka_lq(14, 7, 128, 130)
+    lo, _, _ = oracle.kkt_solve(lq.astype(np.float32).astype(np.float64))
+    _, _, st_cold = parity(lq)
+    e_lam, _, st = parity(lq, lam0=gen.warm_start(lo, 130, 0, rel=1e-5))
+    assert st["status"][0] == 0 and e_lam < TOL_F32
+    assert st["iters"][0] < st_cold["iters"][0]
+
+
+def test_exact_warm_start_takes_zero_iterations():
+    lq = gen.kuka_lq(4, 2, 6, 2)
+    lo, _, _ = oracle.kkt_solve(lq.astype(np.float64))
+    from paper_2309_08079_gb300.solver import make_opts
+    _, _, _, st, _ = run_gpu(lq, "float64", lam0=lo, opts=make_opts(tol=1e-8))
+    assert st["status"][0] == 0 and st["iters"][0] == 0
+
+
+def test_decoupled_converges_in_one_iteration():
+    """A_k = B_k = 0: Phi^-1 = S+^-1 exactly, so PCG ends after one iteration."""
+    lq = gen.kuka_lq(14, 7, 40, 5)
+    lq.A[:] = 0.0
+    lq.B[:] = 0.0
+    e_lam, e_dz, st = parity(lq)
+    assert st["iters"][0] == 1 and st["status"][0] == 0
+    assert e_lam < 1e-6
+
+
+def test_paper_exit_mode():
+    """tol_mode 1: the paper's absolute test eta' = r^T Phi^-1 r < eps."""
+    from paper_2309_08079_gb300.solver import make_opts
+    lq = gen.kuka_lq(14, 7, 128, 9)
+    _, _, _, st, _ = run_gpu(lq.astype(np.float32), opts=make_opts(tol=1e-4, tol_mode=1))
+    assert st["status"][0] == 0 and st["eta"][0] < 1e-4
+    _, _, _, st2, _ = run_gpu(lq.astype(np.float32), opts=make_opts(tol=1e-6))
+    assert st["iters"][0] < st2["iters"][0]
+
+
+# ------------------------------------------------------------------ statuses
+def test_status_not_converged_keeps_iterate():
+    from paper_2309_08079_gb300.solver import make_opts
+    lq = gen.kuka_lq(14, 7, 64, 3)
+    lam, _, _, st, _ = run_gpu(lq.astype(np.float32), opts=make_opts(max_iter=3))
+    assert st["status"][0] == 1 and st["iters"][0] == 3
+    assert np.all(np.isfinite(lam)) and np.abs(lam).max() > 0
+
+
+def test_status_bad_input():
+    lq = gen.kuka_lq(14, 7, 16, 3)
+    lq.Qd[5, 2] = -1.0
+    lam, _, _, st, _ = run_gpu(lq.astype(np.float32), lam0=np.full((16, 14), 7.0))
+    assert st["status"][0] == 4
+    assert np.all(lam == 7.0)  # left unchanged
+
+
+def test_status_nonfinite():
+    lq = gen.kuka_lq(14, 7, 16, 3)
+    lq.A[4, 1, 1] = np.nan
+    _, _, _, st, _ = run_gpu(lq.astype(np.float32))
+    assert st["status"][0] in (2, 3)
