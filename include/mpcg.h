@@ -61,6 +61,7 @@ extern "C" {
 #define MPCG_EINVAL (-1)       /* bad argument (null pointer, size, dtype) */
 #define MPCG_ECUDA (-2)        /* a CUDA runtime call or launch failed */
 #define MPCG_EUNSUPPORTED (-3) /* shape outside what the kernels support */
+#define MPCG_ETOOLARGE (-4)    /* needs more scratch than MPCG_NOALLOC_SCRATCH_BYTES */
 
 /* numerical status written to mpcg_stats.status */
 #define MPCG_CONVERGED 0
@@ -210,6 +211,40 @@ int mpcg_backward(mpcg_handle *h, mpcg_dims dims, const mpcg_lq *lq, const mpcg_
                   const void *lambda, const void *dx, const void *du, const void *lam_bar,
                   const void *dx_bar, const void *du_bar, const mpcg_grads *grads,
                   const mpcg_opts *opts, mpcg_stats *stats, void *workspace, void *stream);
+
+/*
+ * Backward pass that allocates nothing and takes no workspace (the paper
+ * has no counterpart).
+ *
+ * Who needs it: callers that cannot allocate device memory when they
+ * differentiate -- a controller whose memory is fixed at start-up and
+ * whose control loop must not enter the allocator (an allocation can take
+ * locks and has no bounded latency), or a host framework that owns every
+ * allocation and hands this library only the problem's tensors.  For them
+ * the scratch that mpcg_backward_batched takes as `workspace` (the adjoint
+ * right-hand side, the adjoint solution and the instance queue:
+ * mpcg_workspace_bytes(dims, B) bytes) comes instead from one fixed array
+ * of MPCG_NOALLOC_SCRATCH_BYTES bytes of device memory that the library
+ * reserves when it is loaded; every GPU that loads the library keeps that
+ * array until the process exits.
+ *
+ * Arguments, layouts and results are those of mpcg_backward_batched
+ * (knot_off may be NULL when B == 1).  Behaviour specific to this call:
+ *  - the first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture;
+ *  - a problem whose scratch exceeds MPCG_NOALLOC_SCRATCH_BYTES is refused
+ *    with MPCG_ETOOLARGE before anything is launched;
+ *  - it calls no cudaMalloc, cudaFree or allocating library routine;
+ *  - all calls share the one array, which keeps the last call's contents:
+ *    each call clears what must start at zero, and calls that overlap on
+ *    the GPU (other streams, other host threads) race -- serialise them.
+ */
+#define MPCG_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+int mpcg_backward_batched_noalloc(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
+                                  const mpcg_lq *lq, const mpcg_schur *schur, const void *lambda,
+                                  const void *dx, const void *du, const void *lam_bar,
+                                  const void *dx_bar, const void *du_bar, const mpcg_grads *grads,
+                                  const mpcg_opts *opts, mpcg_stats *stats, void *stream);
 
 #ifdef __cplusplus
 }

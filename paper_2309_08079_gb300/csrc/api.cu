@@ -222,6 +222,7 @@ const char *mpcg_strerror(int code) {
         case MPCG_EINVAL: return "invalid argument";
         case MPCG_ECUDA: return "CUDA runtime or launch error";
         case MPCG_EUNSUPPORTED: return "shape not supported by the kernels";
+        case MPCG_ETOOLARGE: return "problem needs more scratch than the no-allocation entry point holds";
         case MPCG_NOT_CONVERGED: return "not converged within max_iter";
         case MPCG_BREAKDOWN: return "breakdown: p^T S p <= 0 or not finite";
         case MPCG_NONFINITE: return "residual not finite";
@@ -344,3 +345,72 @@ int mpcg_backward(mpcg_handle *h, mpcg_dims d, const mpcg_lq *lq, const mpcg_sch
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Backward pass without a workspace, for callers that cannot allocate device
+// memory when they differentiate (see mpcg_backward_batched_noalloc in
+// include/mpcg.h).  Its scratch is this one file-scope array, reserved when
+// the library is loaded.  Host code cannot use the array's name as a device
+// address, so the address is looked up once per device with
+// cudaGetSymbolAddress while that device is current.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MPCG_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+int noalloc_scratch(mpcg_handle *h, void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return MPCG_ECUDA;
+    }
+    if (dev != h->device) return MPCG_EINVAL;  // the handle belongs to another device
+    if (dev < 0 || dev >= kMaxDevices) return MPCG_EUNSUPPORTED;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return err_cuda(e);
+        if (!p) return MPCG_ECUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return MPCG_OK;
+}
+}  // namespace
+
+extern "C" int mpcg_backward_batched_noalloc(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,
+                                             const mpcg_lq *lq, const mpcg_schur *s,
+                                             const void *lambda, const void *dx, const void *du,
+                                             const void *lam_bar, const void *dx_bar,
+                                             const void *du_bar, const mpcg_grads *g,
+                                             const mpcg_opts *opts, mpcg_stats *stats,
+                                             void *stream) {
+    if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !lambda || !dx ||
+        !lam_bar || !dx_bar || !g || !g->A || !g->B || !g->Qd || !g->Rd || !g->q || !g->r ||
+        !g->c || (d.N > 1 && (!du || !du_bar)))
+        return MPCG_EINVAL;
+    const size_t need = mpcg_workspace_bytes(d, B);
+    if (need == 0) return MPCG_EINVAL;
+    if (need > MPCG_NOALLOC_SCRATCH_BYTES) {
+        std::fprintf(stderr,
+                     "mpcg_backward_batched_noalloc: needs %zu bytes of scratch, holds %zu; "
+                     "use mpcg_backward_batched with a workspace\n",
+                     need, (size_t)MPCG_NOALLOC_SCRATCH_BYTES);
+        return MPCG_ETOOLARGE;
+    }
+    void *ws = nullptr;
+    int rc = noalloc_scratch(h, &ws);
+    if (rc) return rc;
+    if (d.dtype == 1)
+        return backward_t<double>(h, d, B, knot_off, lq, s, (const double *)lambda,
+                                  (const double *)dx, (const double *)du, (const double *)lam_bar,
+                                  (const double *)dx_bar, (const double *)du_bar, g, opts, stats,
+                                  ws, (cudaStream_t)stream);
+    return backward_t<float>(h, d, B, knot_off, lq, s, (const float *)lambda, (const float *)dx,
+                             (const float *)du, (const float *)lam_bar, (const float *)dx_bar,
+                             (const float *)du_bar, g, opts, stats, ws, (cudaStream_t)stream);
+}
