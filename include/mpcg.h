@@ -170,6 +170,25 @@ int mpcg_pcg_solve(mpcg_handle *h, mpcg_dims dims, const mpcg_schur *schur, void
 int mpcg_recover_step(mpcg_handle *h, mpcg_dims dims, const mpcg_lq *lq, const void *lambda,
                       void *dx, void *du, void *stream);
 
+/*
+ * One step of mixed-precision iterative refinement of lambda (no
+ * counterpart in the paper; it lifts the accuracy floor that rounding S+ to
+ * working precision sets).  The exact residual
+ *     b - S+ lambda = -(C dz(lambda) + c),   dz(lambda) = G^-1 (C^T lambda - g),
+ * is formed per knot in extended precision from the inputs `lq` (not from
+ * the stored S+), the correction S+ d = residual is solved by PCG with the
+ * same S+ and Phi^-1 from d = 0, and lambda += d.  `workspace` needs
+ * mpcg_workspace_bytes(dims, B) bytes; `stats` (device) receives the
+ * correction solve's stats (relres is relative to the residual).
+ */
+int mpcg_refine_step(mpcg_handle *h, mpcg_dims dims, const mpcg_lq *lq, const mpcg_schur *schur,
+                     void *lambda, const mpcg_opts *opts, mpcg_stats *stats, void *workspace,
+                     void *stream);
+int mpcg_refine_step_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
+                             const mpcg_lq *lq, const mpcg_schur *schur, void *lambda,
+                             const mpcg_opts *opts, mpcg_stats *stats, void *workspace,
+                             void *stream);
+
 /* Batched forms: B independent instances in one launch each (see knot_off
  * above).  Stats has B entries; pcg_solve_batched needs a workspace of
  * mpcg_workspace_bytes(dims, B) bytes (its instance queue). */

@@ -32,7 +32,7 @@ EXPORTS = (
     "mpcg_form_schur", "mpcg_form_precon", "mpcg_pcg_solve", "mpcg_recover_step",
     "mpcg_form_schur_batched", "mpcg_form_precon_batched", "mpcg_pcg_solve_batched",
     "mpcg_recover_step_batched", "mpcg_backward_batched", "mpcg_backward",
-    "mpcg_backward_batched_noalloc",
+    "mpcg_backward_batched_noalloc", "mpcg_refine_step", "mpcg_refine_step_batched",
 )
 
 
@@ -112,6 +112,12 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.mpcg_backward.restype = i32
     lib.mpcg_backward.argtypes = [vp, mpcg_dims, P(mpcg_lq), P(mpcg_schur), vp, vp, vp, vp, vp,
                                   vp, P(mpcg_grads), P(mpcg_opts), vp, vp, vp]
+    lib.mpcg_refine_step.restype = i32
+    lib.mpcg_refine_step.argtypes = [vp, mpcg_dims, P(mpcg_lq), P(mpcg_schur), vp, P(mpcg_opts), vp,
+                                     vp, vp]
+    lib.mpcg_refine_step_batched.restype = i32
+    lib.mpcg_refine_step_batched.argtypes = [vp, mpcg_dims, i32, vp, P(mpcg_lq), P(mpcg_schur), vp,
+                                             P(mpcg_opts), vp, vp, vp]
     lib.mpcg_backward_batched_noalloc.restype = i32
     lib.mpcg_backward_batched_noalloc.argtypes = [vp, mpcg_dims, i32, vp, P(mpcg_lq), P(mpcg_schur), vp,
                                                   vp, vp, vp, vp, vp, P(mpcg_grads), P(mpcg_opts), vp,

@@ -203,6 +203,27 @@ int recover_t(const mpcg_dims &d, int B, const int *knot_off, const mpcg_lq *lq,
                                       (T *)du, st));
 }
 
+template <typename T>
+int refine_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const mpcg_lq *lq,
+             const mpcg_schur *s, T *lam, const mpcg_opts *o, mpcg_stats *stats, void *ws,
+             cudaStream_t st) {
+    BatchView bv = make_bv(knot_off, B, d.N);
+    const int Kgrid = knot_off ? B * d.N : d.N;
+    const size_t vec = al256((size_t)Kgrid * d.nx * sizeof(T));
+    char *w = (char *)ws;
+    T *res = (T *)(w + 256);
+    T *delta = (T *)(w + 256 + vec);
+    int rc = err_cuda(launch_resid<T>(d.nx, d.nu, bv, Kgrid, (const T *)lq->A, (const T *)lq->B,
+                                      (const T *)lq->Qd, (const T *)lq->Rd, (const T *)lq->q,
+                                      (const T *)lq->r, (const T *)lq->c, lam, res, st));
+    if (rc) return rc;
+    rc = err_cuda(cudaMemsetAsync(delta, 0, (size_t)Kgrid * d.nx * sizeof(T), st));
+    if (rc) return rc;
+    rc = pcg_t<T>(h, d, B, knot_off, s, res, T(1), delta, o, stats, ws, st);
+    if (rc) return rc;
+    return err_cuda(launch_axpy<T>(d.nx, bv, Kgrid, delta, lam, st));
+}
+
 // Per-control arrays (A, B, Rd, r) are empty, and may be NULL, when every
 // horizon is 1 (dims.N == 1).
 bool lq_ok(const mpcg_lq *lq, const mpcg_dims &d) {
@@ -314,6 +335,26 @@ int mpcg_recover_step_batched(mpcg_handle *h, mpcg_dims d, int B, const int *kno
 int mpcg_recover_step(mpcg_handle *h, mpcg_dims d, const mpcg_lq *lq, const void *lambda, void *dx,
                       void *du, void *stream) {
     return mpcg_recover_step_batched(h, d, 1, nullptr, lq, lambda, dx, du, stream);
+}
+
+int mpcg_refine_step_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,
+                             const mpcg_lq *lq, const mpcg_schur *s, void *lambda,
+                             const mpcg_opts *opts, mpcg_stats *stats, void *workspace,
+                             void *stream) {
+    if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !s->Sd ||
+        !s->Pd || (d.N > 1 && (!s->So || !s->Po)) || !lambda || !workspace)
+        return MPCG_EINVAL;
+    if (d.dtype == 1)
+        return refine_t<double>(h, d, B, knot_off, lq, s, (double *)lambda, opts, stats, workspace,
+                                (cudaStream_t)stream);
+    return refine_t<float>(h, d, B, knot_off, lq, s, (float *)lambda, opts, stats, workspace,
+                           (cudaStream_t)stream);
+}
+
+int mpcg_refine_step(mpcg_handle *h, mpcg_dims d, const mpcg_lq *lq, const mpcg_schur *s,
+                     void *lambda, const mpcg_opts *opts, mpcg_stats *stats, void *workspace,
+                     void *stream) {
+    return mpcg_refine_step_batched(h, d, 1, nullptr, lq, s, lambda, opts, stats, workspace, stream);
 }
 
 int mpcg_backward_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,

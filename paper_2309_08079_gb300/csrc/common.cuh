@@ -47,6 +47,25 @@ __device__ __forceinline__ dfloat df_add_lazy(dfloat a, dfloat b) {
     return dfloat{s, __fadd_rn(__fadd_rn(a.lo, b.lo), e)};
 }
 
+// float-pair times a float, renormalised
+__device__ __forceinline__ dfloat df_mul_f(dfloat x, float b) {
+    float p = __fmul_rn(x.hi, b);
+    float e = __fmaf_rn(x.hi, b, -p);
+    e = __fmaf_rn(x.lo, b, e);
+    float hi = __fadd_rn(p, e);
+    return dfloat{hi, __fsub_rn(e, __fsub_rn(hi, p))};
+}
+
+// float-pair divided by a float (one correction step)
+__device__ __forceinline__ dfloat df_div_f(dfloat x, float b) {
+    float q1 = __fdiv_rn(x.hi, b);
+    dfloat p = df_prod(q1, b);
+    float r = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo);
+    float q2 = __fdiv_rn(r, b);
+    float hi = __fadd_rn(q1, q2);
+    return dfloat{hi, __fsub_rn(q2, __fsub_rn(hi, q1))};
+}
+
 template <typename T>
 struct Acc;
 
@@ -68,6 +87,13 @@ struct Acc<float> {
         return (double)a.hi + (double)a.lo;
     }
     __device__ static __forceinline__ float to_T(dfloat a) { return __fadd_rn(a.hi, a.lo); }
+    __device__ static __forceinline__ dfloat from(float a) { return dfloat{a, 0.f}; }
+    __device__ static __forceinline__ dfloat neg(dfloat a) { return dfloat{-a.hi, -a.lo}; }
+    // acc + a * x for a float a and an extended x
+    __device__ static __forceinline__ dfloat fma_x(float a, dfloat x, dfloat acc) {
+        return df_add(acc, df_mul_f(x, a));
+    }
+    __device__ static __forceinline__ dfloat div_x(dfloat x, float b) { return df_div_f(x, b); }
 };
 
 template <>
@@ -84,6 +110,10 @@ struct Acc<double> {
     __device__ static __forceinline__ double bcast0(double a) { return __shfl_sync(0xffffffffu, a, 0); }
     __device__ static __forceinline__ double to_double(double a) { return a; }
     __device__ static __forceinline__ double to_T(double a) { return a; }
+    __device__ static __forceinline__ double from(double a) { return a; }
+    __device__ static __forceinline__ double neg(double a) { return -a; }
+    __device__ static __forceinline__ double fma_x(double a, double x, double acc) { return __fma_rn(a, x, acc); }
+    __device__ static __forceinline__ double div_x(double x, double b) { return x / b; }
 };
 
 template <typename T>

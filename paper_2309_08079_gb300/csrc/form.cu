@@ -7,6 +7,7 @@
 // stages that knot's small blocks in shared memory; G = 32 (one warp) for
 // nx <= 16 and 128 otherwise.  Knots of a ragged batch are numbered
 // globally; a group finds its instance by binary search over knot_off.
+#include <algorithm>
 #include <type_traits>
 
 #include "launch.cuh"
@@ -235,20 +236,23 @@ recover_kernel(int nx, int nu, BatchView bv, const T *__restrict__ A,
     const int j = kg - b;
     for (int i = t; i < nx; i += G) vn[i] = last ? T(0) : v[(size_t)(kg + 1) * nx + i];
     group_sync(G);
+    // v_k - A_k^T v_{k+1} - hx_k cancels heavily when v is large against z:
+    // accumulate with exact products and an extended sum, round once.
+    using AT = Acc<T>;
     for (int i = t; i < nx + nu; i += G) {
         if (i < nx) {
-            T s = v[(size_t)kg * nx + i] - hx[(size_t)kg * nx + i];
+            auto s = AT::add(AT::from(v[(size_t)kg * nx + i]), AT::from(-hx[(size_t)kg * nx + i]));
             if (!last) {
                 const T *Ak = A + (size_t)j * nx * nx;
-                for (int m = 0; m < nx; ++m) s -= Ak[m * nx + i] * vn[m];
+                for (int m = 0; m < nx; ++m) s = AT::add(s, AT::prod(-Ak[m * nx + i], vn[m]));
             }
-            zx[(size_t)kg * nx + i] = s / Qd[(size_t)kg * nx + i];
+            zx[(size_t)kg * nx + i] = AT::to_T(AT::div_x(s, Qd[(size_t)kg * nx + i]));
         } else if (!last) {
             const int u = i - nx;
             const T *Bk = B + (size_t)j * nx * nu;
-            T s = -hu[(size_t)j * nu + u];
-            for (int m = 0; m < nx; ++m) s -= Bk[m * nu + u] * vn[m];
-            zu[(size_t)j * nu + u] = s / Rd[(size_t)j * nu + u];
+            auto s = AT::from(-hu[(size_t)j * nu + u]);
+            for (int m = 0; m < nx; ++m) s = AT::add(s, AT::prod(-Bk[m * nu + u], vn[m]));
+            zu[(size_t)j * nu + u] = AT::to_T(AT::div_x(s, Rd[(size_t)j * nu + u]));
         }
     }
 }
@@ -338,6 +342,86 @@ grad_kernel(int nx, int nu, BatchView bv, const T *__restrict__ lam,
 }
 
 // ---------------------------------------------------------------------------
+// Exact-operator residual for iterative refinement.  For S+ = C G^-1 C^T and
+// b = -gamma = C G^-1 g - c, the residual of a multiplier estimate is
+//     b - S+ lambda = -(C dz(lambda) + c),   dz(lambda) = G^-1 (C^T lambda - g),
+// i.e. the defect of the linearised dynamics at the recovered step.  It is
+// formed per knot in extended precision straight from the inputs, so it
+// carries neither the rounding of S+ to working precision nor the drift of
+// the PCG recurrences.  Block row k:
+//   k = 0: -(dx_0 + c_0)
+//   k > 0: A_{k-1} dx_{k-1} + B_{k-1} du_{k-1} - dx_k - c_k
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(FORM_THREADS)
+resid_kernel(int nx, int nu, BatchView bv, const T *__restrict__ A, const T *__restrict__ B,
+             const T *__restrict__ Qd, const T *__restrict__ Rd, const T *__restrict__ q,
+             const T *__restrict__ r, const T *__restrict__ c, const T *__restrict__ lam,
+             T *__restrict__ out) {
+    using AT = Acc<T>;
+    using X = typename AT::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = group_size(nx);
+    const int groups = FORM_THREADS / G;
+    const int g = threadIdx.x / G, t = threadIdx.x % G;
+    const int kg = blockIdx.x * groups + g;
+    X *xs = reinterpret_cast<X *>(smem_raw) + (size_t)g * (2 * nx + nu);
+    X *dx_cur = xs, *dx_prev = xs + nx, *du_prev = xs + 2 * nx;
+    if (kg >= bv.total()) return;
+    const int b = bv.owner(kg);
+    int k0, Nb;
+    bv.range(b, k0, Nb);
+    const int k = kg - k0;
+    const bool last = k + 1 >= Nb;
+    // dz entries of this knot (dx_k) and of the previous one (dx_{k-1}, du_{k-1})
+    for (int i = t; i < nx; i += G) {
+        X s = AT::from(lam[(size_t)kg * nx + i]);
+        s = AT::add(s, AT::from(-q[(size_t)kg * nx + i]));
+        if (!last) {
+            const T *Ak = A + (size_t)(kg - b) * nx * nx;
+            for (int m = 0; m < nx; ++m) s = AT::add(s, AT::prod(-Ak[m * nx + i], lam[(size_t)(kg + 1) * nx + m]));
+        }
+        dx_cur[i] = AT::div_x(s, Qd[(size_t)kg * nx + i]);
+    }
+    if (k > 0) {
+        const int j = kg - b - 1;
+        const T *Ap = A + (size_t)j * nx * nx;
+        const T *Bp = B + (size_t)j * nx * nu;
+        for (int i = t; i < nx; i += G) {
+            X s = AT::from(lam[(size_t)(kg - 1) * nx + i]);
+            s = AT::add(s, AT::from(-q[(size_t)(kg - 1) * nx + i]));
+            for (int m = 0; m < nx; ++m) s = AT::add(s, AT::prod(-Ap[m * nx + i], lam[(size_t)kg * nx + m]));
+            dx_prev[i] = AT::div_x(s, Qd[(size_t)(kg - 1) * nx + i]);
+        }
+        for (int i = t; i < nu; i += G) {
+            X s = AT::from(-r[(size_t)j * nu + i]);
+            for (int m = 0; m < nx; ++m) s = AT::add(s, AT::prod(-Bp[m * nu + i], lam[(size_t)kg * nx + m]));
+            du_prev[i] = AT::div_x(s, Rd[(size_t)j * nu + i]);
+        }
+    }
+    group_sync(G);
+    for (int i = t; i < nx; i += G) {
+        X s = AT::add(AT::neg(dx_cur[i]), AT::from(-c[(size_t)kg * nx + i]));
+        if (k > 0) {
+            const int j = kg - b - 1;
+            const T *Ap = A + (size_t)j * nx * nx;
+            const T *Bp = B + (size_t)j * nx * nu;
+            for (int m = 0; m < nx; ++m) s = AT::fma_x(Ap[i * nx + m], dx_prev[m], s);
+            for (int m = 0; m < nu; ++m) s = AT::fma_x(Bp[i * nu + m], du_prev[m], s);
+        }
+        out[(size_t)kg * nx + i] = AT::to_T(s);
+    }
+}
+
+// lam[i] += d[i] over every knot of the batch
+template <typename T>
+__global__ void axpy_kernel(int nx, BatchView bv, const T *__restrict__ d, T *__restrict__ lam) {
+    const size_t n = (size_t)bv.total() * nx;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        lam[i] += d[i];
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
 static inline int form_grid(int nx, int Ktot) {
@@ -396,6 +480,25 @@ cudaError_t launch_grad(int nx, int nu, BatchView bv, int Kgrid, const T *lam, c
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_resid(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B, const T *Qd,
+                         const T *Rd, const T *q, const T *r, const T *c, const T *lam, T *out,
+                         cudaStream_t s) {
+    using X = typename Acc<T>::type;
+    const int groups = FORM_THREADS / group_size(nx);
+    resid_kernel<T><<<form_grid(nx, Kgrid), FORM_THREADS, sizeof(X) * (2 * nx + nu) * groups, s>>>(
+        nx, nu, bv, A, B, Qd, Rd, q, r, c, lam, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_axpy(int nx, BatchView bv, int Kgrid, const T *d, T *lam, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = std::max(1, std::min(1024, ceil_div(Kgrid * nx, threads)));
+    axpy_kernel<T><<<blocks, threads, 0, s>>>(nx, bv, d, lam);
+    return cudaGetLastError();
+}
+
 // Raise every per-knot kernel's dynamic shared-memory ceiling once per device
 // (large nx needs more than the 48 KB default).
 template <typename T>
@@ -406,6 +509,7 @@ static cudaError_t form_prepare_t(int smem_optin) {
     if ((e = cudaFuncSetAttribute(precon_inv_kernel<T>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(precon_off_kernel<T>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(recover_kernel<T>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(resid_kernel<T>, a, smem_optin))) return e;
     return cudaFuncSetAttribute(cgh_kernel<T>, a, smem_optin);
 }
 
@@ -426,7 +530,11 @@ cudaError_t form_prepare(int smem_optin) {
                                        cudaStream_t);                                             \
     template cudaError_t launch_grad<T>(int, int, BatchView, int, const T *, const T *,           \
                                         const T *, const T *, const T *, const T *, T *, T *,     \
-                                        T *, T *, T *, cudaStream_t);
+                                        T *, T *, T *, cudaStream_t);                             \
+    template cudaError_t launch_resid<T>(int, int, BatchView, int, const T *, const T *,          \
+                                         const T *, const T *, const T *, const T *, const T *,   \
+                                         const T *, T *, cudaStream_t);                           \
+    template cudaError_t launch_axpy<T>(int, BatchView, int, const T *, T *, cudaStream_t);
 MPCG_INST(float)
 MPCG_INST(double)
 #undef MPCG_INST

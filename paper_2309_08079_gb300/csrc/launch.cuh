@@ -60,6 +60,12 @@ template <typename T>
 cudaError_t launch_grad(int nx, int nu, BatchView bv, int Kgrid, const T *lam, const T *mu,
                         const T *dx, const T *du, const T *gq, const T *gr, T *gA, T *gB, T *gQd,
                         T *gRd, T *gc, cudaStream_t s);
+template <typename T>
+cudaError_t launch_resid(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B, const T *Qd,
+                         const T *Rd, const T *q, const T *r, const T *c, const T *lam, T *out,
+                         cudaStream_t s);
+template <typename T>
+cudaError_t launch_axpy(int nx, BatchView bv, int Kgrid, const T *d, T *lam, cudaStream_t s);
 template <typename T> cudaError_t pcg_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
 template <typename T> int pcg_max_clusters(const PcgLaunch &);
 cudaError_t pcg_prepare(int smem_optin);

@@ -205,11 +205,33 @@ class Solver:
         L.check("mpcg_recover_step", rc)
         return dx, du
 
+    def refine_step(self, lq: LQTensors, schur: SchurTensors, lam: torch.Tensor, opts=None,
+                    stats: Optional[torch.Tensor] = None, workspace=None, stream=None):
+        """One step of iterative refinement of lam (in place) with the exact residual."""
+        ss, ls = schur.struct(), lq.lq_struct()
+        o = opts if opts is not None else make_opts()
+        if stats is None:
+            stats = self.alloc_stats(lq.nb, lq.device)
+        if workspace is None:
+            workspace = self.alloc_workspace(lq)
+        if lq.batched:
+            rc = self.lib.mpcg_refine_step_batched(self.h, lq.dims(), lq.nb, _ptr(lq.knot_off),
+                                                   C.byref(ls), C.byref(ss), _ptr(lam), C.byref(o),
+                                                   _ptr(stats), _ptr(workspace), _stream(stream))
+        else:
+            rc = self.lib.mpcg_refine_step(self.h, lq.dims(), C.byref(ls), C.byref(ss), _ptr(lam),
+                                           C.byref(o), _ptr(stats), _ptr(workspace), _stream(stream))
+        L.check("mpcg_refine_step", rc)
+        return stats
+
     def solve(self, lq: LQTensors, lam0: Optional[torch.Tensor] = None, opts=None,
-              schur: Optional[SchurTensors] = None, stats=None, workspace=None, stream=None):
-        """The whole path: form_schur, form_precon, pcg_solve, recover_step.
+              schur: Optional[SchurTensors] = None, stats=None, workspace=None, stream=None,
+              refine: int = 0):
+        """The whole path: form_schur, form_precon, pcg_solve, `refine` steps of
+        iterative refinement, recover_step.
 
         Returns (lam, dx, du, stats, schur); lam0 (if given) is overwritten.
+        stats are those of the first PCG solve.
         """
         if schur is None:
             schur = self.alloc_schur(lq)
@@ -218,6 +240,12 @@ class Solver:
         self.form_schur(lq, schur, stream)
         self.form_precon(lq, schur, stream)
         stats = self.pcg_solve(lq, schur, lam, opts, stats, workspace, stream)
+        if refine > 0:
+            if workspace is None:
+                workspace = self.alloc_workspace(lq)
+            rstats = self.alloc_stats(lq.nb, lq.device)
+            for _ in range(refine):
+                self.refine_step(lq, schur, lam, opts, rstats, workspace, stream)
         dx, du = self.recover_step(lq, lam, stream=stream)
         return lam, dx, du, stats, schur
 

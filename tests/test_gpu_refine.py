@@ -1,0 +1,85 @@
+"""Iterative refinement with the exact-operator residual (mpcg_refine_step)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import TOL_F32, oracle_solution, parity, run_gpu, solver
+from workload import gen
+
+pytestmark = pytest.mark.gpu
+
+LARGE = gen.CONFIG_LARGE
+
+
+def _solve(lq32, refine, dtype="float32", lam0=None):
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    s = solver()
+    lt = LQTensors.from_numpy(lq32)
+    lam = None if lam0 is None else torch.as_tensor(lam0, dtype=torch.float32, device="cuda").clone()
+    lam, dx, du, st, _ = s.solve(lt, lam, opts=make_opts(), refine=refine)
+    torch.cuda.synchronize()
+    return lam.cpu().double().numpy(), dx.cpu().double().numpy(), du.cpu().double().numpy(), read_stats(st)
+
+
+def _errs(lq32, lam, dx, du):
+    lo, xo, uo = oracle_solution(lq32)
+    return (oracle.relerr(lam, lo),
+            oracle.relerr(np.concatenate([dx.ravel(), du.ravel()]), np.concatenate([xo.ravel(), uo.ravel()])))
+
+
+# After refinement lambda is exact to about its float32 storage; dz is
+# recovered from that float32 lambda through a cancelling difference, so
+# it is held to the float32 parity bar.
+@pytest.mark.parametrize("N", [64, 128, 256])
+def test_refinement_on_the_large_state(N):
+    """nx = 36 with the large-state generator (dt = 0.005, Qd ~ U[0.1, 100])."""
+    lq = gen.kuka_lq(36, 12, N, LARGE["seed_base"] + N, dt=LARGE["dt"], qd=LARGE["qd"]).astype(np.float32)
+    e0 = _errs(lq, *_solve(lq, 0)[:3])
+    e1 = _errs(lq, *_solve(lq, 1)[:3])
+    e2 = _errs(lq, *_solve(lq, 2)[:3])
+    assert e1[0] < 1e-6 and e2[0] < 1e-6, (e0, e1, e2)
+    assert e1[1] < TOL_F32 and e2[1] < TOL_F32, (e0, e1, e2)
+
+
+def test_refinement_on_the_n512_workload():
+    lq = gen.kuka_lq(14, 7, 512, 514).astype(np.float32)
+    e0 = _errs(lq, *_solve(lq, 0)[:3])
+    e1 = _errs(lq, *_solve(lq, 1)[:3])
+    assert max(e0) < TOL_F32 and e1[0] < 1e-6 and e1[1] < e0[1], (e0, e1)
+
+
+def test_refinement_keeps_an_exact_solution():
+    """At lambda = the exact solution the exact residual is at rounding level,
+    so a refinement step leaves lambda where it is."""
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts
+    s = solver()
+    lq = gen.kuka_lq(14, 7, 40, 77).astype(np.float32)
+    lo, _, _ = oracle_solution(lq)
+    lt = LQTensors.from_numpy(lq)
+    sch = s.alloc_schur(lt)
+    s.form_schur(lt, sch)
+    s.form_precon(lt, sch)
+    lam = torch.as_tensor(lo, dtype=torch.float32, device="cuda").contiguous()
+    s.refine_step(lt, sch, lam, make_opts())
+    torch.cuda.synchronize()
+    assert oracle.relerr(lam.cpu().double().numpy(), lo) < 1e-6
+
+
+def test_refinement_batched():
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts
+    s = solver()
+    batch = gen.kuka_batch(36, 12, [64, 20, 100], LARGE["seed_base"], dt=LARGE["dt"],
+                           qd=LARGE["qd"]).astype(np.float32)
+    lt = LQTensors.from_batch(batch)
+    lam, dx, du, st, _ = s.solve(lt, opts=make_opts(), refine=2, workspace=s.alloc_workspace(lt))
+    torch.cuda.synchronize()
+    lam, dx, du = (t.cpu().double().numpy() for t in (lam, dx, du))
+    ko, co = batch.knot_off, batch.ctrl_off()
+    for b, it in enumerate(batch.items):
+        lo, xo, uo = oracle_solution(it)
+        assert oracle.relerr(lam[ko[b]:ko[b + 1]], lo) < 1e-6
+        z = np.concatenate([dx[ko[b]:ko[b + 1]].ravel(), du[co[b]:co[b + 1]].ravel()])
+        assert oracle.relerr(z, np.concatenate([xo.ravel(), uo.ravel()])) < TOL_F32
