@@ -158,6 +158,19 @@ def oracle_baseline(lq, seconds: float):
     return el / n * 1e6, n
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value over the ranks of the default process group (the job's
+    time is its slowest rank's); the value itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    dev = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # --------------------------------------------------------------------- reference arm
 def run_reference(args, rank):
     if rank != 0:
@@ -252,11 +265,7 @@ def run_ours(args, rank, world, local_rank):
     step_ms = [ev[i][0].elapsed_time(ev[i][3]) for i in timed]
     pcg_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in timed]
     form_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in timed]
-    tot_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(float(np.sum(step_ms)), dev)
     st = read_stats(stats)[args.warmup:]
     converged = bool(np.all(st["status"] == 0))
     iters = st["iters"].astype(np.float64)
@@ -288,9 +297,10 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": "pcg_cluster_kernel", "peak_source": peak_note,
                 "alg_bytes_per_launch": alg_bytes, "launch_us": pcg_s * 1e6}
 
-    batched = None
+    batched = backward = None
     if not args.no_batched:
         batched = run_batched(s, dev, args.batched_solves)
+        backward = run_backward(s, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -315,7 +325,7 @@ def run_ours(args, rank, world, local_rank):
         "converged": converged,
         "parity": {"err_lambda": err_lam, "err_dz": err_dz, "tol": 1e-4},
         "clocks": clk, "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roofline,
-        "cpu_baseline": cpu, "batched": batched,
+        "cpu_baseline": cpu, "batched": batched, "backward": backward,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -396,39 +406,47 @@ def run_batched(s, dev, solves):
         for w, m in zip(work, master):
             w.copy_(m)
 
-    def body():
+    def body(opts_m):
         for r in range(solves):
             s.form_schur(lt, sch)
             s.form_precon(lt, sch)
-            s.pcg_solve(lt, sch, work[r], opts, stats[r], ws)
+            s.pcg_solve(lt, sch, work[r], opts_m, stats[r], ws)
             s.recover_step(lt, work[r], dx, du)
 
-    # capture the repeated solves in one graph
-    restore()
-    body()  # warm-up outside capture (sets launch attributes)
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    side = torch.cuda.Stream(dev)
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        with torch.cuda.graph(g, stream=side):
-            body()
-    torch.cuda.current_stream().wait_stream(side)
-    times = []
-    for _ in range(3):
+    # capture the repeated solves in one graph, once per PCG kernel form
+    per_mode = {}
+    for mode, name in ((1, "cluster"), (2, "cta")):
+        om = make_opts(tol=1e-6, mode=mode)
         restore()
+        body(om)  # warm-up outside capture (chooses the launch shape)
         torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        g.replay()
-        b.record()
-        b.synchronize()
-        times.append(a.elapsed_time(b))
-    t_graph = float(np.median(times)) / 1e3
-    stb = np.concatenate([read_stats(x) for x in stats])
-    ok_b = bool(np.all(stb["status"] == 0))
-    iters_b = float(np.mean(stb["iters"]))
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                body(om)
+        torch.cuda.current_stream().wait_stream(side)
+        times = []
+        for _ in range(3):
+            restore()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        stb = np.concatenate([read_stats(x) for x in stats])
+        per_mode[name] = {"graph_ms": float(np.median(times)),
+                          "converged": bool(np.all(stb["status"] == 0)),
+                          "mean_iters": float(np.mean(stb["iters"]))}
+        del g
+    best = min(per_mode, key=lambda k: per_mode[k]["graph_ms"])
+    t_graph = per_mode[best]["graph_ms"] / 1e3
+    ok_b = all(v["converged"] for v in per_mode.values())
+    iters_b = per_mode[best]["mean_iters"]
 
     # plain loop: the single-instance path over the same solves
     items = [LQTensors.from_numpy(it, device=dev) for it in batch.items]
@@ -453,8 +471,82 @@ def run_batched(s, dev, solves):
     return {"workload": f"{batch.B} instances, N_i ~ U{{{c['N_lo']}..{c['N_hi']}}} "
                         f"(sum {int(ko[-1])} knots), {solves} warm solves each",
             "solves_per_s": n / t_graph, "loop_solves_per_s": n / t_loop,
-            "speedup_vs_loop": t_loop / t_graph, "graph_ms": t_graph * 1e3,
+            "speedup_vs_loop": t_loop / t_graph, "graph_ms": t_graph * 1e3, "kernel": best,
+            "per_kernel": {k: {"solves_per_s": n / (v["graph_ms"] / 1e3), **v} for k, v in per_mode.items()},
             "mean_iters": iters_b, "converged": ok_b, "cold_iters_mean": float(np.mean(read_stats(st0)["iters"]))}
+
+
+def run_backward(s, dev, reps=5):
+    """Forward + backward of the gradient workload (64 instances, N = 128,
+    loss sum ||dz||^2 + w^T lambda): batched calls vs the single-instance
+    path looped over the same instances."""
+    import torch
+    import oracle
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    c = gen.CONFIG_GRAD
+    batch = gen.kuka_batch(c["nx"], c["nu"], [c["N"]] * c["B"], c["seed_base"], dt=c["dt"],
+                           qd=c["qd"]).astype(np.float32)
+    lt = LQTensors.from_batch(batch, device=dev)
+    K = lt.total
+    w = torch.as_tensor(gen.loss_weights(K * c["nx"], c["w_seed"]).reshape(K, c["nx"]),
+                        dtype=torch.float32, device=dev)
+    opts = make_opts(tol=1e-6)
+    sch = s.alloc_schur(lt)
+    ws = s.alloc_workspace(lt)
+    st = s.alloc_stats(lt.nb, dev)
+    lam = torch.zeros(K, c["nx"], device=dev)
+
+    def fwd():
+        lam.zero_()
+        return s.solve(lt, lam, opts=opts, schur=sch, stats=st, workspace=ws)
+
+    def bwd(lam_, dx, du):
+        return s.backward(lt, sch, lam_, dx, du, w, 2 * dx, 2 * du, opts=opts, workspace=ws)
+
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b), out
+
+    fwd_ms, bwd_ms = [], []
+    for i in range(reps + 1):
+        tf, (lam_o, dx, du, _, _) = timed(fwd)
+        tb, (g, bst) = timed(lambda: bwd(lam_o, dx, du))
+        if i:
+            fwd_ms.append(tf)
+            bwd_ms.append(tb)
+    ok = bool(np.all(read_stats(bst)["status"] == 0))
+    # gradient of instance 0 against the oracle's analytic gradient
+    it0 = batch.items[0].astype(np.float64)
+    l0, x0, u0 = oracle.kkt_solve(it0)
+    w0 = w[:c["N"]].double().cpu().numpy()
+    go = oracle.grad(it0, l0, x0, u0, w0, 2 * x0, 2 * u0)
+    gerr = max(oracle.relerr(g["A"][:c["N"] - 1].double().cpu().numpy(), go["A"]),
+               oracle.relerr(g["Qd"][:c["N"]].double().cpu().numpy(), go["Qd"]),
+               oracle.relerr(g["c"][:c["N"]].double().cpu().numpy(), go["c"]))
+    # looped single-instance forward + backward
+    items = [LQTensors.from_numpy(it, device=dev) for it in batch.items]
+    schs = [s.alloc_schur(it) for it in items]
+    wss = [s.alloc_workspace(it) for it in items]
+    ko = batch.knot_off
+
+    def loop():
+        for bi, it in enumerate(items):
+            lam_i = torch.zeros(it.total, it.nx, device=dev)
+            l_, dx_, du_, _, _ = s.solve(it, lam_i, opts=opts, schur=schs[bi])
+            s.backward(it, schs[bi], l_, dx_, du_, w[ko[bi]:ko[bi + 1]], 2 * dx_, 2 * du_, opts=opts,
+                       workspace=wss[bi])
+
+    timed(loop)
+    t_loop = float(np.median([timed(loop)[0] for _ in range(3)]))
+    f, bw = float(np.median(fwd_ms)), float(np.median(bwd_ms))
+    return {"workload": f"{c['B']} instances x N={c['N']} (nx={c['nx']}, nu={c['nu']}), loss sum ||dz||^2 + w^T lambda",
+            "fwd_ms": f, "bwd_ms": bw, "bwd_over_fwd": bw / f, "loop_fwd_bwd_ms": t_loop,
+            "speedup_vs_loop": t_loop / (f + bw), "converged": ok, "grad_relerr_vs_oracle": gerr}
 
 
 def main():

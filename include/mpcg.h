@@ -94,7 +94,10 @@ typedef struct {
                       1: paper's eta' = r^T Phi^-1 r < tol (Algorithm 1) */
     int max_iter;  /* <= 0: 10 N nx */
     int cluster;   /* CTAs per instance (1..16); 0 = automatic */
-    int reserved;
+    int mode;      /* PCG kernel: 0 automatic; 1 a thread-block cluster per instance
+                      (latency: matrices held on chip); 2 one CTA per instance
+                      (throughput for batches: matrices streamed from L2, many
+                      instances at once, any horizon that fits shared memory) */
 } mpcg_opts;
 
 typedef struct {

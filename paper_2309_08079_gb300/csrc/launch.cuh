@@ -37,6 +37,7 @@ struct PcgParams {
 };
 
 struct PcgLaunch {
+    int cta_mode;  // 1: one CTA per instance (pcg_cta_kernel); 0: cluster per instance
     int C;         // CTAs per cluster
     int clusters;  // clusters in the grid
     int threads;   // threads per CTA
@@ -69,6 +70,10 @@ cudaError_t launch_axpy(int nx, BatchView bv, int Kgrid, const T *d, T *lam, cud
 template <typename T> cudaError_t pcg_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
 template <typename T> int pcg_max_clusters(const PcgLaunch &);
 cudaError_t pcg_prepare(int smem_optin);
+cudaError_t pcg_cta_prepare(int smem_optin);
+template <typename T> size_t pcg_cta_smem_bytes(int nmax, int vs, int W);
+template <typename T> cudaError_t pcg_cta_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
+template <typename T> int pcg_cta_max_blocks(const PcgLaunch &);
 cudaError_t form_prepare(int smem_optin);
 template <typename T> size_t pcg_smem_bytes(int kpc_max, int vs, int C, int W, int nx, int stage);
 

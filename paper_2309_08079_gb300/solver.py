@@ -100,8 +100,9 @@ class SchurTensors:
                                                       self.gamma, self.info)))
 
 
-def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0) -> L.mpcg_opts:
-    return L.mpcg_opts(float(tol), int(tol_mode), int(max_iter), int(cluster), 0)
+def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0, mode=0) -> L.mpcg_opts:
+    """mode: 0 automatic, 1 cluster per instance, 2 one CTA per instance."""
+    return L.mpcg_opts(float(tol), int(tol_mode), int(max_iter), int(cluster), int(mode))
 
 
 def read_stats(stats: torch.Tensor) -> np.ndarray:

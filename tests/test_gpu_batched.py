@@ -34,18 +34,41 @@ def _check(batch, lam, dx, du, st, tol):
         assert e_lam < tol and e_dz < tol, (b, it.N, e_lam, e_dz)
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("Ns", [[1, 5, 32, 33, 100, 64], [512, 3, 257], [2] * 7])
-def test_batched_ragged_parity(Ns):
+def test_batched_ragged_parity(Ns, mode):
+    from paper_2309_08079_gb300.solver import make_opts
     batch = gen.kuka_batch(14, 7, Ns, 1000).astype(np.float32)
-    lam, dx, du, st = _run_batch(batch)
+    lam, dx, du, st = _run_batch(batch, opts=make_opts(mode=mode))
     _check(batch, lam, dx, du, st, TOL_F32)
 
 
-def test_batched_queue_more_instances_than_clusters():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_batched_queue_more_instances_than_clusters(mode):
+    """300 instances: more than the co-resident clusters or CTAs, so the
+    persistent grid drains the instance queue."""
+    from paper_2309_08079_gb300.solver import make_opts
     Ns = gen.batch_horizons(300, 8, 64, 3)
     batch = gen.kuka_batch(14, 7, Ns, 2000).astype(np.float32)
-    lam, dx, du, st = _run_batch(batch)
+    lam, dx, du, st = _run_batch(batch, opts=make_opts(mode=mode))
     _check(batch, lam, dx, du, st, TOL_F32)
+
+
+def test_batched_modes_agree():
+    """The cluster and the CTA-per-instance kernels solve the same batch to
+    the same tolerance; the CTA kernel is deterministic across batch shapes."""
+    from paper_2309_08079_gb300.solver import make_opts
+    from gpu_util import run_gpu
+    Ns = [40, 7, 129, 300]
+    batch = gen.kuka_batch(14, 7, Ns, 56).astype(np.float32)
+    l1, _, _, s1 = _run_batch(batch, opts=make_opts(mode=1))
+    l2, _, _, s2 = _run_batch(batch, opts=make_opts(mode=2))
+    assert oracle.relerr(l1, l2) < 2 * TOL_F32
+    ko = batch.knot_off
+    for b, it in enumerate(batch.items):
+        lone, _, _, st, _ = run_gpu(it, opts=make_opts(mode=2))
+        np.testing.assert_array_equal(l2[ko[b]:ko[b + 1]], lone)
+        assert st["iters"][0] == s2["iters"][b]
 
 
 def test_batched_other_shapes_and_f64():
