@@ -202,8 +202,10 @@ __device__ __forceinline__ void fence_mbar_init() {
 }
 
 // One local arrival that also raises the phase's expected transaction bytes.
+// Relaxed: the arrival publishes no data of its own (the payload completes
+// through st.async transaction bytes), so it orders nothing before it.
 __device__ __forceinline__ void mbar_arrive_expect(uint32_t mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
+    asm volatile("mbarrier.arrive.expect_tx.relaxed.cta.shared::cta.b64 _, [%0], %1;" ::"r"(mbar),
                  "r"(bytes)
                  : "memory");
 }
@@ -226,9 +228,25 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Wait for the phase of `parity` with a deadline; false if it gave up.
+// Non-blocking probe of the phase of `parity` (never suspends the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `parity` with a deadline; false if it gave up.  The
+// first microseconds spin on test_wait (a suspended try_wait can wake late
+// on the critical path); after that try_wait lets the thread sleep.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, uint64_t limit_ns) {
-    if (mbar_try_wait(mbar, parity)) return true;
+    for (int i = 0; i < 4096; ++i)
+        if (mbar_test_wait(mbar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         if (mbar_try_wait(mbar, parity)) return true;
