@@ -1,0 +1,122 @@
+"""Parity at the measured workloads' full sizes, in the launch shapes the
+benchmark uses, on instances the oracle solves one by one."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import TOL_F32, oracle_solution, solver
+from workload import gen
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve_batch(batch, lam0=None, opts=None, refine=0):
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    s = solver()
+    lt = LQTensors.from_batch(batch)
+    lam = None if lam0 is None else torch.as_tensor(lam0, dtype=torch.float32, device="cuda").clone()
+    lam, dx, du, st, _ = s.solve(lt, lam, opts=opts or make_opts(), workspace=s.alloc_workspace(lt),
+                                 refine=refine)
+    torch.cuda.synchronize()
+    return (lam.cpu().double().numpy(), dx.cpu().double().numpy(), du.cpu().double().numpy(),
+            read_stats(st))
+
+
+def _check_sample(batch, lam, dx, du, st, picks, tol_lam, tol_dz):
+    ko, co = batch.knot_off, batch.ctrl_off()
+    assert np.all(st["status"] == 0), np.unique(st["status"], return_counts=True)
+    for b in picks:
+        lo, xo, uo = oracle_solution(batch.items[b])
+        e_lam = oracle.relerr(lam[ko[b]:ko[b + 1]], lo)
+        z = np.concatenate([dx[ko[b]:ko[b + 1]].ravel(), du[co[b]:co[b + 1]].ravel()])
+        e_dz = oracle.relerr(z, np.concatenate([xo.ravel(), uo.ravel()]))
+        assert e_lam < tol_lam and e_dz < tol_dz, (b, batch.Ns[b], e_lam, e_dz)
+
+
+def test_sweep_warm_started_every_horizon():
+    """Latency sweep: N in {64, 128, 256, 512}, seed 2 + N, warm start from
+    the converged solution perturbed by 1% relative noise."""
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts
+    c = gen.CONFIG_SWEEP
+    s = solver()
+    for N in c["Ns"]:
+        lq = gen.kuka_lq(c["nx"], c["nu"], N, c["seed_base"] + N, dt=c["dt"], qd=c["qd"]).astype(np.float32)
+        lt = LQTensors.from_numpy(lq)
+        lam_star, _, _, _, sch = s.solve(lt, opts=make_opts())
+        ls = lam_star.cpu().double().numpy()
+        lo, xo, uo = oracle_solution(lq)
+        for rep in range(3):
+            lam0 = torch.as_tensor(gen.warm_start(ls, c["seed_base"] + N, rep), dtype=torch.float32,
+                                   device="cuda")
+            lam, dx, du, st, _ = s.solve(lt, lam0, opts=make_opts(), schur=sch)
+            torch.cuda.synchronize()
+            e_lam = oracle.relerr(lam.cpu().double().numpy(), lo)
+            e_dz = oracle.relerr(np.concatenate([dx.cpu().double().numpy().ravel(),
+                                                 du.cpu().double().numpy().ravel()]),
+                                 np.concatenate([xo.ravel(), uo.ravel()]))
+            assert e_lam < TOL_F32 and e_dz < TOL_F32, (N, rep, e_lam, e_dz)
+
+
+def test_batch256_full_size():
+    """256 instances, N_i ~ U{32..512}, warm-started as in the benchmark."""
+    c = gen.CONFIG_BATCH
+    Ns = gen.batch_horizons(c["B"], c["N_lo"], c["N_hi"], c["n_seed"])
+    batch = gen.kuka_batch(c["nx"], c["nu"], Ns, c["seed_base"], dt=c["dt"], qd=c["qd"]).astype(np.float32)
+    lam_star, _, _, st0 = _solve_batch(batch)
+    ko = batch.knot_off
+    lam0 = np.concatenate([gen.warm_start(lam_star[ko[b]:ko[b + 1]], c["seed_base"] + b, 0)
+                           for b in range(batch.B)])
+    lam, dx, du, st = _solve_batch(batch, lam0=lam0)
+    picks = [int(np.argmin(Ns)), int(np.argmax(Ns))] + list(range(0, batch.B, 37))
+    _check_sample(batch, lam, dx, du, st, picks, TOL_F32, TOL_F32)
+
+
+@pytest.mark.slow
+def test_large_state_batch_full_size():
+    """nx = 36, nu = 12, 1024 instances with N_i ~ U{64..256}, dt = 0.005,
+    Qd ~ U[0.1, 100]; one refinement step as in the large-state reading."""
+    c = gen.CONFIG_LARGE
+    Ns = gen.batch_horizons(c["B"], c["N_lo"], c["N_hi"], c["n_seed"])
+    batch = gen.kuka_batch(c["nx"], c["nu"], Ns, c["seed_base"], dt=c["dt"], qd=c["qd"]).astype(np.float32)
+    picks = [int(np.argmin(Ns)), int(np.argmax(Ns)), 19] + list(range(0, batch.B, 211))
+    # each refinement step contracts the error by about the plain float32
+    # error of the instance (up to ~3e-3 here): one step meets the parity
+    # bar, two go below 1e-6
+    lam, dx, du, st = _solve_batch(batch, refine=1)
+    _check_sample(batch, lam, dx, du, st, picks, TOL_F32, TOL_F32)
+    lam, dx, du, st = _solve_batch(batch, refine=2)
+    _check_sample(batch, lam, dx, du, st, picks, 1e-6, TOL_F32)
+
+
+def test_gradient_batch_full_size():
+    """64 instances x N = 128: backward against the oracle's analytic
+    gradient on sampled instances."""
+    import torch
+    from paper_2309_08079_gb300.autograd import MPCGSolve
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts
+    c = gen.CONFIG_GRAD
+    s = solver()
+    batch = gen.kuka_batch(c["nx"], c["nu"], [c["N"]] * c["B"], c["seed_base"], dt=c["dt"],
+                           qd=c["qd"]).astype(np.float32)
+    lt = LQTensors.from_batch(batch)
+    fields = ("A", "B", "Qd", "Rd", "q", "r", "c")
+    leaves = {f: getattr(lt, f).clone().requires_grad_(True) for f in fields}
+    cfg = dict(solver=s, nx=lt.nx, nu=lt.nu, N=lt.N, knot_off=lt.knot_off, nb=lt.nb, total=lt.total,
+               opts=make_opts(), workspace=s.alloc_workspace(lt))
+    lam, dx, du, _ = MPCGSolve.apply(*(leaves[f] for f in fields), None, cfg)
+    K = lt.total
+    w = gen.loss_weights(K * c["nx"], c["w_seed"]).reshape(K, c["nx"])
+    wt = torch.as_tensor(w, dtype=torch.float32, device="cuda")
+    ((dx * dx).sum() + (du * du).sum() + (wt * lam).sum()).backward()
+    torch.cuda.synchronize()
+    g = {f: leaves[f].grad.cpu().double().numpy() for f in fields}
+    ko, co = batch.knot_off, batch.ctrl_off()
+    for b in (0, 17, 63):
+        it = batch.items[b].astype(np.float64)
+        lo, xo, uo = oracle.kkt_solve(it)
+        go = oracle.grad(it, lo, xo, uo, w[ko[b]:ko[b + 1]], 2 * xo, 2 * uo)
+        for f in fields:
+            sl = slice(co[b], co[b + 1]) if f in ("A", "B", "Rd", "r") else slice(ko[b], ko[b + 1])
+            assert oracle.relerr(g[f][sl], go[f]) < 1e-3, (b, f)
