@@ -415,7 +415,7 @@ def run_batched(s, dev, solves):
 
     # capture the repeated solves in one graph, once per PCG kernel form
     per_mode = {}
-    for mode, name in ((1, "cluster"), (2, "cta")):
+    for mode, name in ((1, "cluster"), (2, "cta_l2"), (3, "cta_tma")):
         om = make_opts(tol=1e-6, mode=mode)
         restore()
         body(om)  # warm-up outside capture (chooses the launch shape)

@@ -95,9 +95,13 @@ typedef struct {
     int max_iter;  /* <= 0: 10 N nx */
     int cluster;   /* CTAs per instance (1..16); 0 = automatic */
     int mode;      /* PCG kernel: 0 automatic; 1 a thread-block cluster per instance
-                      (latency: matrices held on chip); 2 one CTA per instance
-                      (throughput for batches: matrices streamed from L2, many
-                      instances at once, any horizon that fits shared memory) */
+                      (matrices held on chip; the automatic choice whenever the
+                      horizon fits); 2 one CTA per instance reading the blocks
+                      from L2 (many instances at once, any horizon that fits
+                      shared memory; the automatic choice beyond a cluster);
+                      3 one CTA per instance with the blocks staged into shared
+                      memory by TMA bulk copies (needs 16-byte multiples and
+                      16-byte-aligned block arrays, else as 2) */
 } mpcg_opts;
 
 typedef struct {

@@ -1,6 +1,7 @@
 // C ABI of the solve path (include/mpcg.h): argument checks, launch-shape
 // selection and stream-ordered launches.  No call allocates memory.
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -72,6 +73,35 @@ int choose_pcg_cta(mpcg_handle *h, const mpcg_dims &d, int B, PcgLaunch &L) {
     return MPCG_OK;
 }
 
+// Launch shape of the TMA-staged CTA-per-instance kernel; MPCG_EUNSUPPORTED
+// when its bulk copies cannot be used (a block size or a block array not
+// 16-byte aligned) or its shared memory does not fit.
+template <typename T>
+int choose_pcg_stream(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_schur *s, PcgLaunch &L) {
+    const int nx = d.nx;
+    if (nx <= 16) { L.lpk = 16; L.rpt = 1; }
+    else if (nx <= 32) { L.lpk = 32; L.rpt = 1; }
+    else if (nx <= 64) { L.lpk = 32; L.rpt = 2; }
+    else return MPCG_EUNSUPPORTED;
+    const size_t blk = sizeof(T) * (size_t)nx * nx;
+    if (blk % 16 != 0) return MPCG_EUNSUPPORTED;
+    for (const void *ptr : {s->Sd, s->So, s->Pd, s->Po})
+        if (ptr && ((uintptr_t)ptr % 16) != 0) return MPCG_EUNSUPPORTED;
+    L.cta_mode = 2;
+    L.C = 1;
+    L.mode = MODE_PTR;
+    L.stage = 0;
+    L.threads = 256;
+    L.vs = nx <= 16 ? 16 : ceil_div(nx, 4) * 4;
+    L.kpc_max = d.N;
+    L.smem = pcg_stream_smem_bytes<T>(d.N, L.vs, L.threads / 32, nx, L.threads / L.lpk);
+    if (L.smem > (size_t)h->smem_optin) return MPCG_EUNSUPPORTED;
+    const int per_sm = pcg_stream_max_blocks<T>(L);
+    if (per_sm < 1) return MPCG_EUNSUPPORTED;
+    L.clusters = std::max(1, std::min(B, per_sm * h->sms));
+    return MPCG_OK;
+}
+
 // Launch shape of the cluster PCG kernel for horizons up to Nmax.
 template <typename T>
 int choose_pcg_cluster(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, PcgLaunch &L) {
@@ -115,13 +145,19 @@ int choose_pcg_cluster(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opt
 }
 
 // Kernel choice: a cluster per instance whenever the horizon fits one
-// (measured faster for single solves and for the 256-instance ragged batch:
-// 5.5k vs 4.7k solves/s), one CTA per instance for horizons beyond what a
-// 16-CTA cluster holds, or when asked for.
+// (measured fastest for single solves and for the 256-instance ragged batch:
+// 5.8k solves/s vs 4.7k with one CTA per instance reading L2 and 2.8k with
+// TMA-staged blocks), one CTA per instance for horizons beyond what a 16-CTA
+// cluster holds, or when asked for.
 template <typename T>
-int choose_pcg(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, PcgLaunch &L) {
+int choose_pcg(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, const mpcg_schur *s,
+               PcgLaunch &L) {
     const int mode = o ? o->mode : 0;
     if (mode == 2) return choose_pcg_cta<T>(h, d, B, L);
+    if (mode == 3) {
+        if (choose_pcg_stream<T>(h, d, B, s, L) == MPCG_OK) return MPCG_OK;
+        return choose_pcg_cta<T>(h, d, B, L);
+    }
     if (mode == 1) return choose_pcg_cluster<T>(h, d, B, o, L);
     int rc = choose_pcg_cluster<T>(h, d, B, o, L);
     if (rc == MPCG_EUNSUPPORTED && !(o && o->cluster > 0)) return choose_pcg_cta<T>(h, d, B, L);
@@ -156,12 +192,15 @@ int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const 
     int rc = MPCG_OK;
     {
         std::lock_guard<std::mutex> g(h->mu);
-        auto key = std::make_tuple(d.dtype, d.nx, d.N, B, (o ? o->cluster : 0) | ((o ? o->mode : 0) << 8));
+        // the streaming kernel's eligibility depends on pointer alignment
+        const int aligned = (((uintptr_t)s->Sd | (uintptr_t)s->So | (uintptr_t)s->Pd | (uintptr_t)s->Po) % 16) == 0;
+        auto key = std::make_tuple(d.dtype, d.nx, d.N, B,
+                                   (o ? o->cluster : 0) | ((o ? o->mode : 0) << 8) | (aligned << 16));
         auto it = h->shapes.find(key);
         if (it != h->shapes.end()) {
             L = it->second;
         } else {
-            rc = choose_pcg<T>(h, d, B, o, L);
+            rc = choose_pcg<T>(h, d, B, o, s, L);
             if (rc == MPCG_OK) h->shapes.emplace(key, L);
         }
     }
@@ -186,7 +225,8 @@ int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const 
         rc = err_cuda(cudaMemsetAsync(ws, 0, sizeof(int), st));
         if (rc) return rc;
     }
-    if (L.cta_mode) return err_cuda(pcg_cta_launch<T>(L, P, st));
+    if (L.cta_mode == 2) return err_cuda(pcg_stream_launch<T>(L, P, st));
+    if (L.cta_mode == 1) return err_cuda(pcg_cta_launch<T>(L, P, st));
     return err_cuda(pcg_launch<T>(L, P, st));
 }
 
@@ -305,6 +345,7 @@ int mpcg_create(mpcg_handle **out) {
         return MPCG_ECUDA;
     }
     if (pcg_prepare(h->smem_optin) != cudaSuccess || pcg_cta_prepare(h->smem_optin) != cudaSuccess ||
+        pcg_stream_prepare(h->smem_optin) != cudaSuccess ||
         form_prepare(h->smem_optin) != cudaSuccess) {
         cudaGetLastError();
         delete h;

@@ -280,6 +280,17 @@ __device__ __forceinline__ void st_async_v4(uint32_t addr, float a, float b, flo
         : "memory");
 }
 
+// Bulk (TMA, 1-D) copy of `bytes` from global to this CTA's shared memory,
+// completing on `mbar`.  Both addresses 16-byte aligned, bytes % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void *src_gmem, uint32_t bytes,
+                                         uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst_smem),
+        "l"(__cvta_generic_to_global(src_gmem)), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Ragged batches: instance b owns knots [knot_off[b], knot_off[b+1]) and
 // controls [knot_off[b] - b, knot_off[b+1] - b - 1).  A single instance is

@@ -37,7 +37,9 @@ struct PcgParams {
 };
 
 struct PcgLaunch {
-    int cta_mode;  // 1: one CTA per instance (pcg_cta_kernel); 0: cluster per instance
+    int cta_mode;  // 0: cluster per instance; 1: one CTA per instance, blocks from L2
+                   // (pcg_cta_kernel); 2: one CTA per instance, blocks staged by TMA
+                   // (pcg_stream_kernel)
     int C;         // CTAs per cluster
     int clusters;  // clusters in the grid
     int threads;   // threads per CTA
@@ -71,6 +73,10 @@ template <typename T> cudaError_t pcg_launch(const PcgLaunch &, const PcgParams<
 template <typename T> int pcg_max_clusters(const PcgLaunch &);
 cudaError_t pcg_prepare(int smem_optin);
 cudaError_t pcg_cta_prepare(int smem_optin);
+cudaError_t pcg_stream_prepare(int smem_optin);
+template <typename T> size_t pcg_stream_smem_bytes(int nmax, int vs, int W, int nx, int KC);
+template <typename T> cudaError_t pcg_stream_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
+template <typename T> int pcg_stream_max_blocks(const PcgLaunch &);
 template <typename T> size_t pcg_cta_smem_bytes(int nmax, int vs, int W);
 template <typename T> cudaError_t pcg_cta_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
 template <typename T> int pcg_cta_max_blocks(const PcgLaunch &);

@@ -101,7 +101,9 @@ class SchurTensors:
 
 
 def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0, mode=0) -> L.mpcg_opts:
-    """mode: 0 automatic, 1 cluster per instance, 2 one CTA per instance."""
+    """mode: 0 automatic, 1 cluster per instance, 2 one CTA per instance
+    reading blocks from L2, 3 one CTA per instance with TMA-staged blocks
+    (as 2 when blocks are not 16-byte multiples)."""
     return L.mpcg_opts(float(tol), int(tol_mode), int(max_iter), int(cluster), int(mode))
 
 

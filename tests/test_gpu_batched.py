@@ -34,7 +34,7 @@ def _check(batch, lam, dx, du, st, tol):
         assert e_lam < tol and e_dz < tol, (b, it.N, e_lam, e_dz)
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 @pytest.mark.parametrize("Ns", [[1, 5, 32, 33, 100, 64], [512, 3, 257], [2] * 7])
 def test_batched_ragged_parity(Ns, mode):
     from paper_2309_08079_gb300.solver import make_opts
@@ -43,7 +43,7 @@ def test_batched_ragged_parity(Ns, mode):
     _check(batch, lam, dx, du, st, TOL_F32)
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_batched_queue_more_instances_than_clusters(mode):
     """300 instances: more than the co-resident clusters or CTAs, so the
     persistent grid drains the instance queue."""
@@ -63,7 +63,8 @@ def test_batched_modes_agree():
     batch = gen.kuka_batch(14, 7, Ns, 56).astype(np.float32)
     l1, _, _, s1 = _run_batch(batch, opts=make_opts(mode=1))
     l2, _, _, s2 = _run_batch(batch, opts=make_opts(mode=2))
-    assert oracle.relerr(l1, l2) < 2 * TOL_F32
+    l3, _, _, s3 = _run_batch(batch, opts=make_opts(mode=3))
+    assert oracle.relerr(l1, l2) < 2 * TOL_F32 and oracle.relerr(l2, l3) < 2 * TOL_F32
     ko = batch.knot_off
     for b, it in enumerate(batch.items):
         lone, _, _, st, _ = run_gpu(it, opts=make_opts(mode=2))

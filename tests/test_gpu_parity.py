@@ -147,15 +147,19 @@ def test_paper_exit_mode():
 
 
 # ------------------------------------------------------------------ CTA-per-instance kernel
+@pytest.mark.parametrize("mode", [2, 3])
 @pytest.mark.parametrize("nx,nu,N,dtype", [(14, 7, 1, "float32"), (14, 7, 2, "float32"),
-                                           (14, 7, 33, "float32"), (14, 7, 256, "float32"),
-                                           (14, 7, 512, "float32"), (4, 2, 47, "float32"),
+                                           (14, 7, 17, "float32"), (14, 7, 33, "float32"),
+                                           (14, 7, 256, "float32"), (14, 7, 512, "float32"),
+                                           (2, 1, 9, "float32"), (4, 2, 47, "float32"),
                                            (36, 12, 40, "float32"), (14, 7, 200, "float64")])
-def test_cta_mode_parity(nx, nu, N, dtype):
+def test_cta_mode_parity(nx, nu, N, dtype, mode):
+    """One CTA per instance: L2 reads (mode 2) and TMA-staged blocks (mode 3);
+    N = 17 and 33 leave ragged last chunks of the 16-knot stream."""
     from paper_2309_08079_gb300.solver import make_opts
     lq = gen.kuka_lq(nx, nu, N, 600 + N + nx)
     tol = TOL_F32 if dtype == "float32" else TOL_F64
-    e_lam, e_dz, st = parity(lq, dtype=dtype, opts=make_opts(mode=2, tol=1e-6 if dtype == "float32" else 1e-13))
+    e_lam, e_dz, st = parity(lq, dtype=dtype, opts=make_opts(mode=mode, tol=1e-6 if dtype == "float32" else 1e-13))
     assert st["status"][0] == 0, st
     assert e_lam < tol and e_dz < tol, (e_lam, e_dz)
 
@@ -168,15 +172,20 @@ def test_long_horizon_falls_back_to_cta_mode():
     assert st["status"][0] == 0 and e_lam < TOL_F32 and e_dz < TOL_F32, (e_lam, e_dz)
 
 
-def test_cta_mode_statuses():
+@pytest.mark.parametrize("mode", [2, 3])
+def test_cta_mode_statuses(mode):
     from paper_2309_08079_gb300.solver import make_opts
     lq = gen.kuka_lq(14, 7, 64, 3)
-    lam, _, _, st, _ = run_gpu(lq.astype(np.float32), opts=make_opts(max_iter=3, mode=2))
+    lam, _, _, st, _ = run_gpu(lq.astype(np.float32), opts=make_opts(max_iter=3, mode=mode))
     assert st["status"][0] == 1 and st["iters"][0] == 3
     bad = lq.copy()
     bad.Qd[5, 2] = -1.0
-    lam, _, _, st, _ = run_gpu(bad.astype(np.float32), lam0=np.full((64, 14), 7.0), opts=make_opts(mode=2))
+    lam, _, _, st, _ = run_gpu(bad.astype(np.float32), lam0=np.full((64, 14), 7.0), opts=make_opts(mode=mode))
     assert st["status"][0] == 4 and np.all(lam == 7.0)
+    # the exact solution as warm start: converged before the first iteration
+    lo, _, _ = oracle.kkt_solve(lq.astype(np.float32).astype(np.float64))
+    _, _, _, st, _ = run_gpu(lq.astype(np.float32), lam0=lo, opts=make_opts(mode=mode, tol=1e-3))
+    assert st["status"][0] == 0 and st["iters"][0] == 0
 
 
 # ------------------------------------------------------------------ statuses
