@@ -381,6 +381,7 @@ def run_batched(s, dev, solves):
     """256 ragged instances, `solves` warm solves each: one CUDA graph of
     batched calls vs the single-instance path looped on the same GPU."""
     import torch
+    from paper_2309_08079_gb300.autotune import Autotuner, PlanRunner
     from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
     c = gen.CONFIG_BATCH
     Ns = gen.batch_horizons(c["B"], c["N_lo"], c["N_hi"], c["n_seed"])
@@ -410,13 +411,23 @@ def run_batched(s, dev, solves):
         for r in range(solves):
             s.form_schur(lt, sch)
             s.form_precon(lt, sch)
-            s.pcg_solve(lt, sch, work[r], opts_m, stats[r], ws)
+            if isinstance(opts_m, PlanRunner):
+                opts_m.pcg_solve(sch, work[r], stats[r])
+            else:
+                s.pcg_solve(lt, sch, work[r], opts_m, stats[r], ws)
             s.recover_step(lt, work[r], dx, du)
+
+    # the autotuner times its candidate launch plans on the first warm start
+    # (a fresh cache, so every run tunes) and the chosen plan is graphed too
+    with tempfile.TemporaryDirectory() as td:
+        tuner = Autotuner(s, cache_path=os.path.join(td, "tune.json"), reps=3)
+        tuned = tuner.tune(lt, sch, master[0], opts)
+        runner = tuner.runner(lt, sch, master[0], opts)
 
     # capture the repeated solves in one graph, once per PCG kernel form
     per_mode = {}
-    for mode, name in ((1, "cluster"), (2, "cta_l2"), (3, "cta_tma")):
-        om = make_opts(tol=1e-6, mode=mode)
+    for mode, name in ((1, "cluster"), (2, "cta_l2"), (3, "cta_tma"), (runner, "autotuned")):
+        om = make_opts(tol=1e-6, mode=mode) if isinstance(mode, int) else mode
         restore()
         body(om)  # warm-up outside capture (chooses the launch shape)
         torch.cuda.synchronize()
@@ -473,6 +484,8 @@ def run_batched(s, dev, solves):
             "solves_per_s": n / t_graph, "loop_solves_per_s": n / t_loop,
             "speedup_vs_loop": t_loop / t_graph, "graph_ms": t_graph * 1e3, "kernel": best,
             "per_kernel": {k: {"solves_per_s": n / (v["graph_ms"] / 1e3), **v} for k, v in per_mode.items()},
+            "autotune": {"plan": tuned["plan"], "groups": len(runner.launches),
+                         "one_solve_ms": {k: round(v, 3) for k, v in tuner.last_timings.items()}},
             "mean_iters": iters_b, "converged": ok_b, "cold_iters_mean": float(np.mean(read_stats(st0)["iters"]))}
 
 

@@ -102,6 +102,12 @@ typedef struct {
                       3 one CTA per instance with the blocks staged into shared
                       memory by TMA bulk copies (needs 16-byte multiples and
                       16-byte-aligned block arrays, else as 2) */
+    /* Batched PCG only: solve just the instances listed (a DEVICE int
+       array of n_instances distinct indices into the batch); NULL solves
+       all B.  With a list, dims.N may be the largest horizon among the
+       listed instances, which sizes the launch. */
+    const int *instances;
+    int n_instances;
 } mpcg_opts;
 
 typedef struct {
@@ -197,8 +203,12 @@ int mpcg_refine_step_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *k
                              void *stream);
 
 /* Batched forms: B independent instances in one launch each (see knot_off
- * above).  Stats has B entries; pcg_solve_batched needs a workspace of
- * mpcg_workspace_bytes(dims, B) bytes (its instance queue). */
+ * above).  Stats has B entries; pcg_solve_batched takes a workspace of
+ * mpcg_workspace_bytes(dims, B) bytes, of which it uses only the first 256
+ * (its instance queue), so calls that run at once on different streams
+ * (e.g. one per horizon class, each with an instance list in opts) need
+ * 256-byte workspaces of their own.  An instance whose horizon exceeds what
+ * dims.N sized the launch for gets status MPCG_BADINPUT and is not solved. */
 int mpcg_form_schur_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
                             const mpcg_lq *lq, mpcg_schur *schur, void *stream);
 int mpcg_form_precon_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,

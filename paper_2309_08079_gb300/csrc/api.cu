@@ -194,13 +194,14 @@ int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const 
         std::lock_guard<std::mutex> g(h->mu);
         // the streaming kernel's eligibility depends on pointer alignment
         const int aligned = (((uintptr_t)s->Sd | (uintptr_t)s->So | (uintptr_t)s->Pd | (uintptr_t)s->Po) % 16) == 0;
-        auto key = std::make_tuple(d.dtype, d.nx, d.N, B,
+        const int tickets = (o && o->instances && o->n_instances > 0) ? o->n_instances : B;
+        auto key = std::make_tuple(d.dtype, d.nx, d.N, tickets,
                                    (o ? o->cluster : 0) | ((o ? o->mode : 0) << 8) | (aligned << 16));
         auto it = h->shapes.find(key);
         if (it != h->shapes.end()) {
             L = it->second;
         } else {
-            rc = choose_pcg<T>(h, d, B, o, s, L);
+            rc = choose_pcg<T>(h, d, tickets, o, s, L);
             if (rc == MPCG_OK) h->shapes.emplace(key, L);
         }
     }
@@ -219,7 +220,10 @@ int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const 
     P.tol = o ? o->tol : 1e-6;
     P.tol_mode = o ? o->tol_mode : 0;
     P.max_iter = o ? o->max_iter : 0;
-    if (B > 1 && L.clusters < B) {
+    P.inst_list = (o && o->instances && o->n_instances > 0) ? o->instances : nullptr;
+    P.n_tickets = P.inst_list ? o->n_instances : B;
+    if (P.inst_list && !knot_off) return MPCG_EINVAL;
+    if (P.n_tickets > 1 && L.clusters < P.n_tickets) {
         if (!ws) return MPCG_EINVAL;
         P.queue = (int *)ws;
         rc = err_cuda(cudaMemsetAsync(ws, 0, sizeof(int), st));

@@ -28,6 +28,8 @@ struct PcgParams {
     const unsigned *info;
     mpcg_stats *stats;
     int *queue;       // instance counter (nullptr: static round robin)
+    const int *inst_list;  // tickets -> instances (nullptr: ticket t is instance t)
+    int n_tickets;         // instances to solve (B, or the list's length)
     double tol;
     int tol_mode;
     int max_iter;     // <= 0: 10 N nx

@@ -288,12 +288,13 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
             int b;
             if (P.queue) b = atomicAdd(P.queue, 1);
             else b = (int)(cluster_id_x() + (uint32_t)served * num_clusters_x());
+            b = b >= P.n_tickets ? -1 : (P.inst_list ? P.inst_list[b] : b);
             for (uint32_t q = 0; q < C; ++q) st_cluster(map_rank(smem_u32(s_inst), q), b);
         }
         cluster_sync_all();
         const int b = *s_inst;
         ++served;
-        if (b >= P.bv.B) break;
+        if (b < 0) break;
 
         int k0, Nb;
         P.bv.range(b, k0, Nb);
@@ -302,7 +303,8 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
         const int kfirst = (int)rank * KPC;  // instance-local index of slot 0
         const int k = kfirst + kl;            // this thread's knot
         const bool active_knot = kl < KPC && k < Nb;
-        const bool bad = P.info && P.info[b] != 0u;
+        // an instance longer than the launch was sized for is refused
+        const bool bad = (P.info && P.info[b] != 0u) || Nb < 1 || KPC > P.kpc_max;
         const int max_iter = P.max_iter > 0 ? P.max_iter : 10 * Nb * nx;
         const bool send_left = kl == 0 && has_left;
         const bool send_right = kl == KPC - 1 && has_right;
@@ -740,15 +742,18 @@ __global__ void __launch_bounds__(512, 1) pcg_cta_kernel(const PcgParams<T> P) {
 
     int served = 0;
     for (;;) {
-        if (tid == 0) *s_inst = P.queue ? atomicAdd(P.queue, 1) : (int)(blockIdx.x + served * gridDim.x);
+        if (tid == 0) {
+            int t = P.queue ? atomicAdd(P.queue, 1) : (int)(blockIdx.x + served * gridDim.x);
+            *s_inst = t >= P.n_tickets ? -1 : (P.inst_list ? P.inst_list[t] : t);
+        }
         __syncthreads();
         const int b = *s_inst;
         ++served;
-        if (b >= P.bv.B) break;
+        if (b < 0) break;
         int k0, Nb;
         P.bv.range(b, k0, Nb);
         const int c0 = k0 - b;
-        const bool bad = P.info && P.info[b] != 0u;
+        const bool bad = (P.info && P.info[b] != 0u) || Nb < 1 || Nb > P.kpc_max;
         const int max_iter = P.max_iter > 0 ? P.max_iter : 10 * Nb * nx;
         int iters = 0, status = MPCG_CONVERGED;
         A eta = AT::zero(), bb = AT::zero();
@@ -995,15 +1000,18 @@ __global__ void __launch_bounds__(256, 1) pcg_stream_kernel(const PcgParams<T> P
     int served = 0;
     bool failed = false;
     for (;;) {
-        if (tid == 0) s_misc[0] = P.queue ? atomicAdd(P.queue, 1) : (int)(blockIdx.x + served * gridDim.x);
+        if (tid == 0) {
+            int t = P.queue ? atomicAdd(P.queue, 1) : (int)(blockIdx.x + served * gridDim.x);
+            s_misc[0] = t >= P.n_tickets ? -1 : (P.inst_list ? P.inst_list[t] : t);
+        }
         __syncthreads();
         const int b = s_misc[0];
         ++served;
-        if (b >= P.bv.B || failed) break;
+        if (b < 0 || failed) break;
         int k0, Nb;
         P.bv.range(b, k0, Nb);
         const int c0 = k0 - b;
-        const bool bad = P.info && P.info[b] != 0u;
+        const bool bad = (P.info && P.info[b] != 0u) || Nb < 1 || Nb > P.kpc_max;
         const int max_iter = P.max_iter > 0 ? P.max_iter : 10 * Nb * nx;
         const int nch = ceil_div(Nb, KC);
         int iters = 0, status = MPCG_CONVERGED;

@@ -49,6 +49,7 @@ class LQTensors:
     knot_off: Optional[torch.Tensor] = None
     nb: int = 1            # number of instances
     total: int = 0         # total knots
+    Ns: Optional[np.ndarray] = None  # host copy of the horizons (batched)
 
     FIELDS = ("A", "B", "Qd", "Rd", "q", "r", "c")
 
@@ -83,7 +84,8 @@ class LQTensors:
                                 device=device) for f in LQTensors.FIELDS}
         ko = torch.as_tensor(batch.knot_off.astype(np.int32), device=device)
         return LQTensors(batch.nx, batch.nu, int(batch.Ns.max()), **t, knot_off=ko,
-                         nb=batch.B, total=int(batch.knot_off[-1]))
+                         nb=batch.B, total=int(batch.knot_off[-1]),
+                         Ns=np.asarray(batch.Ns, dtype=np.int64).copy())
 
 
 @dataclass
@@ -100,11 +102,15 @@ class SchurTensors:
                                                       self.gamma, self.info)))
 
 
-def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0, mode=0) -> L.mpcg_opts:
+def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0, mode=0, instances=None) -> L.mpcg_opts:
     """mode: 0 automatic, 1 cluster per instance, 2 one CTA per instance
     reading blocks from L2, 3 one CTA per instance with TMA-staged blocks
     (as 2 when blocks are not 16-byte multiples)."""
-    return L.mpcg_opts(float(tol), int(tol_mode), int(max_iter), int(cluster), int(mode))
+    o = L.mpcg_opts(float(tol), int(tol_mode), int(max_iter), int(cluster), int(mode), None, 0)
+    if instances is not None:  # a device int32 tensor of instance indices
+        o.instances = instances.data_ptr()
+        o.n_instances = int(instances.numel())
+    return o
 
 
 def read_stats(stats: torch.Tensor) -> np.ndarray:
@@ -174,8 +180,12 @@ class Solver:
 
     def pcg_solve(self, lq: LQTensors, schur: SchurTensors, lam: torch.Tensor, opts=None,
                   stats: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
-                  stream=None) -> torch.Tensor:
-        """Solve S+ lam = -gamma in place (lam holds the warm start)."""
+                  stream=None, N: Optional[int] = None) -> torch.Tensor:
+        """Solve S+ lam = -gamma in place (lam holds the warm start).
+
+        N (batched calls with an instance list in opts) is the largest
+        horizon among the listed instances; it sizes the launch.
+        """
         ss = schur.struct()
         o = opts if opts is not None else make_opts()
         if stats is None:
@@ -183,7 +193,10 @@ class Solver:
         if lq.batched:
             if workspace is None:
                 workspace = self.alloc_workspace(lq)
-            rc = self.lib.mpcg_pcg_solve_batched(self.h, lq.dims(), lq.nb, _ptr(lq.knot_off),
+            dims = lq.dims()
+            if N is not None:
+                dims.N = int(N)
+            rc = self.lib.mpcg_pcg_solve_batched(self.h, dims, lq.nb, _ptr(lq.knot_off),
                                                  C.byref(ss), _ptr(lam), C.byref(o), _ptr(stats),
                                                  _ptr(workspace), _stream(stream))
         else:

@@ -49,7 +49,7 @@ def test_binding_declares_every_export(lib_path):
 def test_struct_layouts_match_header(lib_path):
     from paper_2309_08079_gb300 import _lib
     assert ctypes.sizeof(_lib.mpcg_stats) == 24
-    assert ctypes.sizeof(_lib.mpcg_opts) == 24
+    assert ctypes.sizeof(_lib.mpcg_opts) == 40
     assert ctypes.sizeof(_lib.mpcg_dims) == 16
     assert ctypes.sizeof(_lib.mpcg_schur) == 6 * ctypes.sizeof(ctypes.c_void_p)
 

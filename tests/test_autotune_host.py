@@ -1,0 +1,58 @@
+"""Host logic of the batched launch-plan autotuner (no GPU)."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_2309_08079_gb300 import autotune as at
+from workload import gen
+
+
+def test_horizon_classes_and_histogram():
+    Ns = np.array([1, 2, 3, 32, 33, 64, 65, 512])
+    assert at.horizon_classes(Ns) == [1, 2, 4, 32, 64, 128, 512]
+    assert at.histogram_key(Ns) == "1:1,2:1,4:1,32:1,64:2,128:1,512:1"
+    assert at.histogram_key(np.array([40, 50, 60])) == "64:3"
+
+
+@pytest.mark.parametrize("Ns", [
+    gen.batch_horizons(256, 32, 512, 3),      # the ragged 256-instance workload
+    np.array([512] * 9),                       # one class
+    np.array([1, 1, 2]),
+    np.array([3, 700, 40, 40, 129]),
+    gen.batch_horizons(1024, 64, 256, 5),
+])
+def test_every_plan_covers_every_instance_once_longest_first(Ns):
+    plans = at.candidate_plans(Ns)
+    assert "single_auto" in plans
+    for name, plan in plans.items():
+        groups = at.group_instances(Ns, plan)
+        idx = np.concatenate([i for _, i in groups])
+        assert sorted(idx.tolist()) == list(range(len(Ns))), name
+        for g, i in groups:
+            assert np.all(np.diff(Ns[i]) <= 0), name        # longest first
+            assert np.all((Ns[i] > g["lo"]) & (Ns[i] <= g["hi"])), name
+            assert g["mode"] in (0, 1, 2, 3)
+
+
+def test_group_instances_rejects_overlap_and_gaps():
+    Ns = np.array([10, 20, 30])
+    with pytest.raises(ValueError):
+        at.group_instances(Ns, [{"lo": 0, "hi": 20, "mode": 0, "cluster": 0},
+                                {"lo": 10, "hi": 40, "mode": 0, "cluster": 0}])
+    with pytest.raises(ValueError):
+        at.group_instances(Ns, [{"lo": 0, "hi": 20, "mode": 0, "cluster": 0}])
+
+
+def test_cache_round_trip(tmp_path):
+    path = tmp_path / "sub" / "tune.json"
+    t = at.Autotuner(solver=None, cache_path=str(path))
+    assert t._load() == {}
+    e = {"plan": "classes_auto", "groups": at.candidate_plans(np.array([5, 50]))["classes_auto"],
+         "ms": 1.5}
+    t._store("k1", e)
+    t._store("k2", {"plan": "single_auto", "groups": [], "ms": 2.0})
+    d = json.loads(path.read_text())
+    assert d["k1"] == e and d["k2"]["plan"] == "single_auto"
+    path.write_text("not json")
+    assert t._load() == {}
