@@ -63,6 +63,10 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--batched-solves", type=int, default=gen.CONFIG_BATCH["solves"])
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-sweep", action="store_true")
+    p.add_argument("--sweep-reps", type=int, default=gen.CONFIG_SWEEP.get("reps", 1000))
+    p.add_argument("--no-large", action="store_true")
+    p.add_argument("--large-solves", type=int, default=gen.CONFIG_LARGE["solves"])
     return p.parse_args()
 
 
@@ -139,6 +143,55 @@ def pcg_traffic_from_profile():
     except Exception:
         pass
     return None
+
+
+def pcg_bytes_per_knot_iter(nx: int, esize: int = 4) -> int:
+    """Algorithmic bytes one PCG iteration moves per knot: both symmetric
+    block-tridiagonal matrices once (T = nx(nx+1)/2 + nx^2 words each) and
+    seven vectors."""
+    T = nx * (nx + 1) // 2 + nx * nx
+    return (2 * T + 7 * nx) * esize
+
+
+def hbm_peak():
+    hbm = measured_peaks().get("hbm_gbs")
+    return (hbm, "of measured") if hbm is not None else (6800.0, "of fallback")
+
+
+def pct(x):
+    x = np.asarray(x, dtype=np.float64)
+    return {"p10": float(np.percentile(x, 10)), "p50": float(np.median(x)),
+            "p90": float(np.percentile(x, 90)), "max": float(np.max(x))}
+
+
+def _oracle_worker(lq64):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.kkt_solve(lq64)
+    return time.perf_counter() - t0
+
+
+def oracle_batched_baseline(items, seconds: float):
+    """FP64 oracle over all host cores, one instance per worker process
+    (a spawned pool: nothing forked after CUDA is initialised), on the first
+    instances of the batch until about `seconds` of wall time."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_worker, [items[0].astype(np.float64)] * cores)  # warm the workers
+        n, t0 = 0, time.perf_counter()
+        while n < len(items):
+            chunk = [it.astype(np.float64) for it in items[n:n + cores]]
+            pool.map(_oracle_worker, chunk)
+            n += len(chunk)
+            if time.perf_counter() - t0 >= seconds:
+                break
+        el = time.perf_counter() - t0
+    return n / el, n, cores
 
 
 def oracle_baseline(lq, seconds: float):
@@ -297,10 +350,24 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": "pcg_cluster_kernel", "peak_source": peak_note,
                 "alg_bytes_per_launch": alg_bytes, "launch_us": pcg_s * 1e6}
 
-    batched = backward = None
+    batched = backward = sweep = exit_sweep = large = None
+    if not args.no_sweep:
+        sweep = run_sweep(s, dev, args.sweep_reps, flush)
+        exit_sweep = run_exit_sweep(s, dev, min(args.sweep_reps, 200))
     if not args.no_batched:
         batched = run_batched(s, dev, args.batched_solves)
         backward = run_backward(s, dev)
+    if not args.no_batched and not args.no_large:
+        large = run_large(s, dev, args.large_solves)
+    if batched is not None and rank == 0 and world == 1 and not args.no_cpu:
+        c = gen.CONFIG_BATCH
+        Ns_b = gen.batch_horizons(c["B"], c["N_lo"], c["N_hi"], c["n_seed"])
+        items = [gen.kuka_lq(c["nx"], c["nu"], int(n), c["seed_base"] + i, dt=c["dt"], qd=c["qd"]).astype(np.float32)
+                 for i, n in enumerate(Ns_b)]
+        rate, n_done, cores = oracle_batched_baseline(items, args.cpu_seconds)
+        batched["cpu_baseline"] = {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                   "sample": f"{n_done} FP64 banded-LU KKT solves of the batch's first instances, "
+                                             f"one per process"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -318,6 +385,7 @@ def run_ours(args, rank, world, local_rank):
                    "seed": SEED, "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "dot_accumulation": "double-float (f32 pair)"},
+        "step_us": pct(np.array(step_ms) * 1e3),
         "step_breakdown_us": {"form": float(np.mean(form_ms)) * 1e3, "pcg": float(np.mean(pcg_ms)) * 1e3,
                               "recover": float(np.mean(step_ms) - np.mean(form_ms) - np.mean(pcg_ms)) * 1e3},
         "pcg_iters": {"mean": float(np.mean(iters)), "min": int(iters.min()), "max": int(iters.max()),
@@ -325,7 +393,8 @@ def run_ours(args, rank, world, local_rank):
         "converged": converged,
         "parity": {"err_lambda": err_lam, "err_dz": err_dz, "tol": 1e-4},
         "clocks": clk, "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roofline,
-        "cpu_baseline": cpu, "batched": batched, "backward": backward,
+        "cpu_baseline": cpu, "batched": batched, "backward": backward, "sweep": sweep,
+        "exit_sweep": exit_sweep, "large_state": large,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -560,6 +629,198 @@ def run_backward(s, dev, reps=5):
     return {"workload": f"{c['B']} instances x N={c['N']} (nx={c['nx']}, nu={c['nu']}), loss sum ||dz||^2 + w^T lambda",
             "fwd_ms": f, "bwd_ms": bw, "bwd_over_fwd": bw / f, "loop_fwd_bwd_ms": t_loop,
             "speedup_vs_loop": t_loop / (f + bw), "converged": ok, "grad_relerr_vs_oracle": gerr}
+
+
+def _step_timer(s, stream):
+    import torch
+
+    class T:
+        def __init__(self):
+            self.ev = []
+
+        def __call__(self, fn):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            self.ev.append((a, b))
+
+        def ms(self):
+            return [a.elapsed_time(b) for a, b in self.ev]
+    return T()
+
+
+def run_sweep(s, dev, reps, flush):
+    """Latency sweep: single instances at N in {64, 128, 256, 512}, each
+    solved `reps` times warm-started from its converged lambda perturbed
+    (seed 2 + N, repetition r); one solve = form_schur, form_precon,
+    pcg_solve, recover_step, L2 flushed before each."""
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    c = gen.CONFIG_SWEEP
+    hbm, note = hbm_peak()
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for N in c["Ns"]:
+        lq = gen.kuka_lq(c["nx"], c["nu"], N, c["seed_base"] + N, dt=c["dt"], qd=c["qd"]).astype(np.float32)
+        lt = LQTensors.from_numpy(lq, device=dev)
+        opts = make_opts(tol=1e-6)
+        sch = s.alloc_schur(lt)
+        lam_star, _, _, _, _ = s.solve(lt, opts=opts, schur=sch)
+        ls = lam_star.cpu().double().numpy()
+        lams = torch.as_tensor(np.stack([gen.warm_start(ls, c["seed_base"] + N, r) for r in range(reps)]),
+                               dtype=torch.float32, device=dev)
+        stats = s.alloc_stats(reps, dev)
+        dx = torch.empty(N, c["nx"], device=dev)
+        du = torch.empty(max(N - 1, 1), c["nu"], device=dev)
+        tim, pcg = _step_timer(s, stream), _step_timer(s, stream)
+
+        def one(r):
+            s.form_schur(lt, sch)
+            s.form_precon(lt, sch)
+            pcg(lambda: s.pcg_solve(lt, sch, lams[r], opts, stats[r * 24:(r + 1) * 24]))
+            s.recover_step(lt, lams[r], dx, du)
+
+        for r in range(min(3, reps)):  # warm-up on copies
+            w = lams[r].clone()
+            s.form_schur(lt, sch)
+            s.form_precon(lt, sch)
+            s.pcg_solve(lt, sch, w, opts)
+        torch.cuda.synchronize()
+        for r in range(reps):
+            flush.zero_()
+            tim(lambda: one(r))
+        torch.cuda.synchronize()
+        st = read_stats(stats)
+        us = np.array(tim.ms()) * 1e3
+        pus = np.array(pcg.ms()) * 1e3
+        it = st["iters"].astype(np.float64)
+        ach = float(np.mean(it)) * N * pcg_bytes_per_knot_iter(c["nx"]) / (np.mean(pus) * 1e-6) / 1e9
+        out[str(N)] = {"us_per_solve": pct(us), "pcg_us": float(np.median(pus)),
+                       "iters": pct(it), "converged": bool(np.all(st["status"] == 0)),
+                       "roofline": {"bound": "hbm", "achieved_gbs": ach, "frac": ach / hbm,
+                                    "peak_source": note}}
+    return {"workload": f"single instances N in {list(c['Ns'])}, nx={c['nx']}, nu={c['nu']}, "
+                        f"{reps} warm solves each (L2 flushed before each)", "per_N": out}
+
+
+def run_exit_sweep(s, dev, reps):
+    """The paper's exit test (absolute eta' = r^T Phi^-1 r < eps, Alg. 1) at
+    eps in {1e-4, 5e-5, 1e-5}, beside the relative-residual default, at
+    N = 128 on warm-started repeat solves: iteration and time
+    distributions and the error each eps leaves against the oracle."""
+    import torch
+    import oracle
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    c = gen.CONFIG_SWEEP
+    N = 128
+    lq = gen.kuka_lq(c["nx"], c["nu"], N, c["seed_base"] + N, dt=c["dt"], qd=c["qd"]).astype(np.float32)
+    lo, _, _ = oracle.kkt_solve(lq.astype(np.float64))
+    lt = LQTensors.from_numpy(lq, device=dev)
+    sch = s.alloc_schur(lt)
+    lam_star, _, _, _, _ = s.solve(lt, opts=make_opts(), schur=sch)
+    ls = lam_star.cpu().double().numpy()
+    lams0 = torch.as_tensor(np.stack([gen.warm_start(ls, c["seed_base"] + N, r) for r in range(reps)]),
+                            dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, o in (("rel_1e-6", make_opts(tol=1e-6)),
+                    ("abs_1e-4", make_opts(tol=1e-4, tol_mode=1)),
+                    ("abs_5e-5", make_opts(tol=5e-5, tol_mode=1)),
+                    ("abs_1e-5", make_opts(tol=1e-5, tol_mode=1))):
+        lams = lams0.clone()
+        stats = s.alloc_stats(reps, dev)
+        s.pcg_solve(lt, sch, lams0[0].clone(), o)       # launch shape chosen outside timing
+        torch.cuda.synchronize()
+        tim = _step_timer(s, stream)
+        for r in range(reps):
+            tim(lambda: s.pcg_solve(lt, sch, lams[r], o, stats[r * 24:(r + 1) * 24]))
+        torch.cuda.synchronize()
+        st = read_stats(stats)
+        errs = [oracle.relerr(lams[r].cpu().double().numpy(), lo) for r in range(0, reps, max(1, reps // 20))]
+        out[name] = {"pcg_us": pct(np.array(tim.ms()) * 1e3), "iters": pct(st["iters"]),
+                     "converged": bool(np.all(st["status"] == 0)),
+                     "err_lambda_vs_oracle": pct(errs)}
+    return {"workload": f"single instance N={N}, nx={c['nx']}, {reps} warm-started PCG solves per exit test",
+            "per_exit": out}
+
+
+def run_large(s, dev, solves):
+    """Large-state batch: nx = 36, nu = 12, 1024 instances with
+    N_i ~ U{64..256}, dt = 0.005, Qd ~ U[0.1, 100].  One step = `solves`
+    warm-started forward solves (each with one refinement step) through the
+    autograd Function and the backward of loss sum ||dz||^2 + w^T lambda over
+    all of them.  The PCG launch plan comes from the autotuner (single-launch
+    plans, so the same launch serves refinement and the adjoint solve)."""
+    import torch
+    import oracle
+    from paper_2309_08079_gb300.autograd import MPCGSolve
+    from paper_2309_08079_gb300.autotune import Autotuner, PlanRunner
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    c = gen.CONFIG_LARGE
+    Ns = gen.batch_horizons(c["B"], c["N_lo"], c["N_hi"], c["n_seed"])
+    batch = gen.kuka_batch(c["nx"], c["nu"], Ns, c["seed_base"], dt=c["dt"], qd=c["qd"]).astype(np.float32)
+    lt = LQTensors.from_batch(batch, device=dev)
+    base = make_opts(tol=1e-6)
+    sch = s.alloc_schur(lt)
+    ws = s.alloc_workspace(lt)
+    s.form_schur(lt, sch)
+    s.form_precon(lt, sch)
+    zero = torch.zeros(lt.total, lt.nx, device=dev)
+    with tempfile.TemporaryDirectory() as td:
+        tuner = Autotuner(s, cache_path=os.path.join(td, "tune.json"), reps=1)
+        best = tuner.tune(lt, sch, zero, base, only=("single_auto", "single_cta_l2", "single_cta_tma"))
+    runner = PlanRunner(s, lt, best["groups"], base)  # owns the instance list opts points at
+    opts = runner.launches[0].opts
+    t0 = time.perf_counter()
+    lam_star, _, _, st0, _ = s.solve(lt, zero.clone(), opts=opts, schur=sch, workspace=ws, refine=1)
+    ls = lam_star.cpu().double().numpy()
+    ko = batch.knot_off
+    lam0 = [torch.as_tensor(np.concatenate([gen.warm_start(ls[ko[b]:ko[b + 1]], c["seed_base"] + b, r)
+                                            for b in range(batch.B)]), dtype=torch.float32, device=dev)
+            for r in range(solves)]
+    K = lt.total
+    w = torch.as_tensor(gen.loss_weights(K * c["nx"], c["seed_base"]).reshape(K, c["nx"]),
+                        dtype=torch.float32, device=dev)
+    leaves = {f: getattr(lt, f).clone().requires_grad_(True) for f in LQTensors.FIELDS}
+    cfg = dict(solver=s, nx=lt.nx, nu=lt.nu, N=lt.N, knot_off=lt.knot_off, nb=lt.nb, total=K,
+               opts=opts, workspace=ws, refine=1)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    outs, loss = [], 0.0
+    for r in range(solves):
+        lam, dx, du, st = MPCGSolve.apply(*(leaves[f] for f in LQTensors.FIELDS), lam0[r], cfg)
+        outs.append((lam, dx, du, st))
+        loss = loss + (dx * dx).sum() + (du * du).sum() + (w * lam).sum()
+    ev[1].record(stream)
+    loss.backward()
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms, bwd_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    sts = np.concatenate([read_stats(o[3]) for o in outs])
+    # per-instance error of the last solve against the FP64 oracle, on a sample
+    lam_l = outs[-1][0].detach().cpu().double().numpy()
+    picks = sorted({int(np.argmin(Ns)), int(np.argmax(Ns))} | set(range(0, batch.B, 128)))
+    errs = {int(b): oracle.relerr(lam_l[ko[b]:ko[b + 1]], oracle.kkt_solve(batch.items[b].astype(np.float64))[0])
+            for b in picks}
+    n = batch.B * solves
+    hbm, note = hbm_peak()
+    it = sts["iters"].astype(np.float64)
+    Nrep = np.tile(Ns, solves)
+    alg = float(np.sum(it * Nrep)) * pcg_bytes_per_knot_iter(c["nx"])
+    return {"workload": f"{batch.B} instances, nx={c['nx']}, nu={c['nu']}, N_i ~ U{{{c['N_lo']}..{c['N_hi']}}} "
+                        f"(sum {int(ko[-1])} knots), {solves} warm solves per step + backward, refine 1",
+            "plan": best["plan"], "tune_ms": {k: round(v, 2) for k, v in tuner.last_timings.items()},
+            "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "solves_per_s_fwd": n / (fwd_ms / 1e3),
+            "solves_per_s_fwd_bwd": n / ((fwd_ms + bwd_ms) / 1e3),
+            "iters_first_pcg": pct(it), "converged": bool(np.all(sts["status"] == 0)),
+            "err_lambda_vs_oracle": {"max": max(errs.values()), "instances": len(errs)},
+            "pcg_roofline_fwd": {"bound": "hbm", "note": "first PCG of each solve only, over the whole forward time",
+                                 "achieved_gbs": alg / (fwd_ms / 1e3) / 1e9,
+                                 "frac": alg / (fwd_ms / 1e3) / 1e9 / hbm, "peak_source": note},
+            "wall_s": time.perf_counter() - t0}
 
 
 def main():

@@ -16,7 +16,8 @@ from .solver import LQTensors, SchurTensors, make_opts
 class MPCGSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, A, B, Qd, Rd, q, r, c, lam0, cfg):
-        """cfg: dict(solver, nx, nu, N, knot_off, nb, total, opts)."""
+        """cfg: dict(solver, nx, nu, N, knot_off, nb, total, opts, workspace,
+        refine) -- refine = steps of iterative refinement after the PCG solve."""
         s = cfg["solver"]
         lq = LQTensors(cfg["nx"], cfg["nu"], cfg["N"], A.contiguous(), B.contiguous(),
                        Qd.contiguous(), Rd.contiguous(), q.contiguous(), r.contiguous(),
@@ -25,7 +26,8 @@ class MPCGSolve(torch.autograd.Function):
         opts = cfg.get("opts") or make_opts()
         lam = lam0.detach().clone() if lam0 is not None else torch.zeros(
             lq.total, lq.nx, dtype=lq.dtype, device=lq.device)
-        lam, dx, du, stats, schur = s.solve(lq, lam, opts=opts, workspace=cfg.get("workspace"))
+        lam, dx, du, stats, schur = s.solve(lq, lam, opts=opts, workspace=cfg.get("workspace"),
+                                            refine=int(cfg.get("refine", 0)))
         ctx.lq_meta = (lq.nx, lq.nu, lq.N, lq.knot_off, lq.nb, lq.total)
         ctx.solver = s
         ctx.opts = opts

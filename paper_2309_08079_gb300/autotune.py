@@ -75,6 +75,15 @@ def candidate_plans(Ns: np.ndarray) -> Dict[str, List[dict]]:
         plans["classes_cta_short"] = short + [
             {"lo": max(a, cut) if short else a, "hi": b, "mode": 0, "cluster": 0}
             for a, b in zip(lo, edges) if b > cut]
+        # finer knots-per-CTA tiling: clusters of ceil(hi / kpc) CTAs holding
+        # kpc knots each, so a smaller CTA shares its SM with another
+        # instance's CTA (classes whose cluster would exceed 16 keep the
+        # library's choice)
+        for kpc in (16, 8):
+            plans[f"classes_kpc{kpc}"] = [
+                {"lo": a, "hi": b, "mode": 0,
+                 "cluster": -(-b // kpc) if -(-b // kpc) <= 16 else 0}
+                for a, b in zip(lo, edges)]
         # two halves of the horizon range
         mid = edges[-1] // 2
         if edges[0] <= mid:
@@ -202,10 +211,10 @@ class Autotuner:
         return float(np.median(times))
 
     def tune(self, lq: LQTensors, schur: SchurTensors, lam0: torch.Tensor, opts=None,
-             store: bool = True) -> dict:
-        """Times every candidate plan on this batch (schur formed, lam0 the
-        warm starts; neither is changed) and returns the fastest entry
-        {"plan": name, "groups": [...], "ms": t}."""
+             store: bool = True, only=None) -> dict:
+        """Times every candidate plan (or those named in `only`) on this batch
+        (schur formed, lam0 the warm starts; neither is changed) and returns
+        the fastest entry {"plan": name, "groups": [...], "ms": t}."""
         from .solver import read_stats
         lam = torch.empty_like(lam0)
         stats = self.solver.alloc_stats(lq.nb, lq.device)
@@ -213,6 +222,8 @@ class Autotuner:
         best = None
         self.last_timings = {}
         for name, groups in candidate_plans(lq.Ns).items():
+            if only is not None and name not in only:
+                continue
             try:
                 runner = PlanRunner(self.solver, lq, groups, opts)
                 t = self._time(runner, schur, lam0, lam, stats)
