@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--sweep-reps", type=int, default=gen.CONFIG_SWEEP.get("reps", 1000))
     p.add_argument("--no-large", action="store_true")
     p.add_argument("--large-solves", type=int, default=gen.CONFIG_LARGE["solves"])
+    p.add_argument("--large-batch", type=int, default=gen.CONFIG_LARGE["B"],
+                   help="instances of the large-state batch (a smaller batch for profiling)")
     return p.parse_args()
 
 
@@ -128,15 +130,22 @@ def measured_peaks():
         return {}
 
 
+def cluster_kernel_sha() -> str:
+    """sha256[:16] over the sources the cluster PCG kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in ("pcg.cu", "pcg_rows.cuh", "common.cuh", "launch.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2309_08079_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def pcg_traffic_from_profile():
     """DRAM bytes per PCG launch from the committed ncu summary, if it was
     captured from the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_2309_08079_gb300", "csrc", "pcg.cu")
     prof = os.path.join(ROOT, "profiles", "pcg_cluster_kernel_N512.md")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = cluster_kernel_sha()
         txt = open(prof).read()
-        m_sha = re.search(r"pcg\.cu sha256\[:16\]:\s*([0-9a-f]+)", txt)
+        m_sha = re.search(r"cluster kernel sources sha256\[:16\]:\s*([0-9a-f]+)", txt)
         m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
         if m_sha and m_tr and m_sha.group(1) == sha:
             return float(m_tr.group(1))
@@ -357,8 +366,8 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_batched:
         batched = run_batched(s, dev, args.batched_solves)
         backward = run_backward(s, dev)
-    if not args.no_batched and not args.no_large:
-        large = run_large(s, dev, args.large_solves)
+    if not args.no_large:
+        large = run_large(s, dev, args.large_solves, args.large_batch)
     if batched is not None and rank == 0 and world == 1 and not args.no_cpu:
         c = gen.CONFIG_BATCH
         Ns_b = gen.batch_horizons(c["B"], c["N_lo"], c["N_hi"], c["n_seed"])
@@ -746,7 +755,7 @@ def run_exit_sweep(s, dev, reps):
             "per_exit": out}
 
 
-def run_large(s, dev, solves):
+def run_large(s, dev, solves, B=None):
     """Large-state batch: nx = 36, nu = 12, 1024 instances with
     N_i ~ U{64..256}, dt = 0.005, Qd ~ U[0.1, 100].  One step = `solves`
     warm-started forward solves (each with one refinement step) through the
@@ -759,7 +768,7 @@ def run_large(s, dev, solves):
     from paper_2309_08079_gb300.autotune import Autotuner, PlanRunner
     from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
     c = gen.CONFIG_LARGE
-    Ns = gen.batch_horizons(c["B"], c["N_lo"], c["N_hi"], c["n_seed"])
+    Ns = gen.batch_horizons(c["B"], c["N_lo"], c["N_hi"], c["n_seed"])[:B or c["B"]]
     batch = gen.kuka_batch(c["nx"], c["nu"], Ns, c["seed_base"], dt=c["dt"], qd=c["qd"]).astype(np.float32)
     lt = LQTensors.from_batch(batch, device=dev)
     base = make_opts(tol=1e-6)
