@@ -73,30 +73,45 @@ int choose_pcg_cta(mpcg_handle *h, const mpcg_dims &d, int B, PcgLaunch &L) {
     return MPCG_OK;
 }
 
-// Launch shape of the TMA-staged CTA-per-instance kernel; MPCG_EUNSUPPORTED
-// when its bulk copies cannot be used (a block size or a block array not
-// 16-byte aligned) or its shared memory does not fit.
+// Launch shape of the tiled CTA-per-instance kernel; MPCG_EUNSUPPORTED when
+// its TMA tiles cannot be used (odd nx: a block is not a 16-byte multiple;
+// a block array not 16-byte aligned; nx > 64) or nothing fits in shared
+// memory.  Each knot stream's steps are bound by their own instruction
+// latency more than by the copies (measured: time falls with the stream
+// count, hardly with the depth), so the launch takes as many streams as fit
+// (at most one per four knots of the longest horizon, at most 16 warps) and
+// then the deepest pipeline (up to 2 steps ahead) that still fits.
 template <typename T>
-int choose_pcg_stream(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_schur *s, PcgLaunch &L) {
+int choose_pcg_tile(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_schur *s, PcgLaunch &L) {
     const int nx = d.nx;
-    if (nx <= 16) { L.lpk = 16; L.rpt = 1; }
-    else if (nx <= 32) { L.lpk = 32; L.rpt = 1; }
-    else if (nx <= 64) { L.lpk = 32; L.rpt = 2; }
-    else return MPCG_EUNSUPPORTED;
-    const size_t blk = sizeof(T) * (size_t)nx * nx;
-    if (blk % 16 != 0) return MPCG_EUNSUPPORTED;
+    if (nx > 64 || nx % 2 != 0) return MPCG_EUNSUPPORTED;
+    if ((sizeof(T) * (size_t)nx * nx) % 16 != 0) return MPCG_EUNSUPPORTED;
     for (const void *ptr : {s->Sd, s->So, s->Pd, s->Po})
         if (ptr && ((uintptr_t)ptr % 16) != 0) return MPCG_EUNSUPPORTED;
     L.cta_mode = 2;
     L.C = 1;
     L.mode = MODE_PTR;
     L.stage = 0;
-    L.threads = 256;
+    L.lpk = nx <= 16 ? 16 : 32;
+    L.rpt = nx <= 32 ? 1 : 2;
+    L.vw = (sizeof(T) == 4 && nx % 4 == 0) ? 4 : 2;
     L.vs = nx <= 16 ? 16 : ceil_div(nx, 4) * 4;
     L.kpc_max = d.N;
-    L.smem = pcg_stream_smem_bytes<T>(d.N, L.vs, L.threads / 32, nx, L.threads / L.lpk);
-    if (L.smem > (size_t)h->smem_optin) return MPCG_EUNSUPPORTED;
-    const int per_sm = pcg_stream_max_blocks<T>(L);
+    const int SW = 32 / L.lpk;
+    const int ns_want = std::max(1, std::min(32, ceil_div(d.N, 4)));
+    int bestW = 0, bestD = 0;
+    for (int W = std::min(16, ceil_div(ns_want, SW)); W >= 1 && !bestW; --W)
+        for (int dep = 2; dep >= 1; --dep)
+            if (pcg_tile_smem_bytes<T>(d.N, L.vs, W, W * SW, nx, dep) <= (size_t)h->smem_optin) {
+                bestW = W;
+                bestD = dep;
+                break;
+            }
+    if (!bestW) return MPCG_EUNSUPPORTED;
+    L.depth = bestD;
+    L.smem = pcg_tile_smem_bytes<T>(d.N, L.vs, bestW, bestW * SW, nx, bestD);
+    L.threads = 32 * bestW;
+    const int per_sm = pcg_tile_max_blocks<T>(L);
     if (per_sm < 1) return MPCG_EUNSUPPORTED;
     L.clusters = std::max(1, std::min(B, per_sm * h->sms));
     return MPCG_OK;
@@ -155,7 +170,7 @@ int choose_pcg(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, co
     const int mode = o ? o->mode : 0;
     if (mode == 2) return choose_pcg_cta<T>(h, d, B, L);
     if (mode == 3) {
-        if (choose_pcg_stream<T>(h, d, B, s, L) == MPCG_OK) return MPCG_OK;
+        if (choose_pcg_tile<T>(h, d, B, s, L) == MPCG_OK) return MPCG_OK;
         return choose_pcg_cta<T>(h, d, B, L);
     }
     if (mode == 1) return choose_pcg_cluster<T>(h, d, B, o, L);
@@ -188,11 +203,11 @@ template <typename T>
 int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const mpcg_schur *s,
           const T *rhs, T sign, T *lam, const mpcg_opts *o, mpcg_stats *stats, void *ws,
           cudaStream_t st) {
-    PcgLaunch L;
+    PcgLaunch L{};
     int rc = MPCG_OK;
     {
         std::lock_guard<std::mutex> g(h->mu);
-        // the streaming kernel's eligibility depends on pointer alignment
+        // the tiled kernel's eligibility depends on pointer alignment
         const int aligned = (((uintptr_t)s->Sd | (uintptr_t)s->So | (uintptr_t)s->Pd | (uintptr_t)s->Po) % 16) == 0;
         const int tickets = (o && o->instances && o->n_instances > 0) ? o->n_instances : B;
         auto key = std::make_tuple(d.dtype, d.nx, d.N, tickets,
@@ -229,7 +244,7 @@ int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const 
         rc = err_cuda(cudaMemsetAsync(ws, 0, sizeof(int), st));
         if (rc) return rc;
     }
-    if (L.cta_mode == 2) return err_cuda(pcg_stream_launch<T>(L, P, st));
+    if (L.cta_mode == 2) return err_cuda(pcg_tile_launch<T>(L, P, st));
     if (L.cta_mode == 1) return err_cuda(pcg_cta_launch<T>(L, P, st));
     return err_cuda(pcg_launch<T>(L, P, st));
 }
@@ -349,7 +364,7 @@ int mpcg_create(mpcg_handle **out) {
         return MPCG_ECUDA;
     }
     if (pcg_prepare(h->smem_optin) != cudaSuccess || pcg_cta_prepare(h->smem_optin) != cudaSuccess ||
-        pcg_stream_prepare(h->smem_optin) != cudaSuccess ||
+        pcg_tile_prepare(h->smem_optin) != cudaSuccess ||
         form_prepare(h->smem_optin) != cudaSuccess) {
         cudaGetLastError();
         delete h;

@@ -282,6 +282,13 @@ __device__ __forceinline__ void st_async_v4(uint32_t addr, float a, float b, flo
 
 // Bulk (TMA, 1-D) copy of `bytes` from global to this CTA's shared memory,
 // completing on `mbar`.  Both addresses 16-byte aligned, bytes % 16 == 0.
+// Orders this thread's (and, after a warp or CTA barrier, its peers')
+// generic-proxy accesses to shared memory before later async-proxy (TMA)
+// writes to the same locations.
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void *src_gmem, uint32_t bytes,
                                          uint32_t mbar) {
     asm volatile(

@@ -36,16 +36,19 @@ struct PcgParams {
     int kpc_max;      // knot slots per CTA (blockDim.x / LPK)
     int stage_smem;   // PTR mode: stage blocks in shared memory
     int vs;           // shared vector stride (elements per knot)
+    int depth;        // pcg_tile_kernel: steps each knot stream copies ahead
 };
 
 struct PcgLaunch {
     int cta_mode;  // 0: cluster per instance; 1: one CTA per instance, blocks from L2
-                   // (pcg_cta_kernel); 2: one CTA per instance, blocks staged by TMA
-                   // (pcg_stream_kernel)
+                   // (pcg_cta_kernel); 2: one CTA per instance, blocks streamed as
+                   // TMA tiles (pcg_tile_kernel)
     int C;         // CTAs per cluster
     int clusters;  // clusters in the grid
     int threads;   // threads per CTA
     int lpk, rpt, mode, stage, vs, kpc_max;
+    int vw;        // pcg_tile_kernel: elements per shared-memory row load (2 or 4)
+    int depth;     // pcg_tile_kernel: steps each knot stream copies ahead (1..4)
     size_t smem;
 };
 
@@ -75,10 +78,10 @@ template <typename T> cudaError_t pcg_launch(const PcgLaunch &, const PcgParams<
 template <typename T> int pcg_max_clusters(const PcgLaunch &);
 cudaError_t pcg_prepare(int smem_optin);
 cudaError_t pcg_cta_prepare(int smem_optin);
-cudaError_t pcg_stream_prepare(int smem_optin);
-template <typename T> size_t pcg_stream_smem_bytes(int nmax, int vs, int W, int nx, int KC);
-template <typename T> cudaError_t pcg_stream_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
-template <typename T> int pcg_stream_max_blocks(const PcgLaunch &);
+cudaError_t pcg_tile_prepare(int smem_optin);
+template <typename T> size_t pcg_tile_smem_bytes(int nmax, int vs, int W, int NS, int nx, int depth);
+template <typename T> cudaError_t pcg_tile_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
+template <typename T> int pcg_tile_max_blocks(const PcgLaunch &);
 template <typename T> size_t pcg_cta_smem_bytes(int nmax, int vs, int W);
 template <typename T> cudaError_t pcg_cta_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
 template <typename T> int pcg_cta_max_blocks(const PcgLaunch &);

@@ -1,6 +1,7 @@
 // One-CTA-per-instance PCG kernels (batched throughput forms of Algorithm 1):
 // pcg_cta_kernel reads the blocks of S+ and Phi^-1 from L2 each iteration;
-// pcg_stream_kernel stages them into shared memory with TMA bulk copies.
+// pcg_tile_kernel streams them through shared memory with TMA bulk copies,
+// one pipeline per knot stream.
 #include <type_traits>
 
 #include "pcg_rows.cuh"
@@ -39,7 +40,7 @@ template <typename T, int LPK, int RPT>
 __global__ void __launch_bounds__(512, 1) pcg_cta_kernel(const PcgParams<T> P) {
     using AT = Acc<T>;
     using A = typename AT::type;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int W = nthreads / 32;
     const int warp = tid / 32, lane = tid % 32;
@@ -252,67 +253,164 @@ __global__ void __launch_bounds__(512, 1) pcg_cta_kernel(const PcgParams<T> P) {
 }
 
 // ---------------------------------------------------------------------------
-// Streaming CTA-per-instance PCG (batched throughput form).  As
-// pcg_cta_kernel, one CTA owns a whole instance with p, r, r~ and S p in
-// shared memory, but the blocks of S+ and Phi^-1 reach shared memory by
-// TMA bulk copies: each pass over the instance (S+ for the matvec, Phi^-1
-// for the preconditioner) is cut into chunks of KC knots whose diagonal and
-// off-diagonal blocks are contiguous in global memory, and chunk q+2 is
-// copied into the stage chunk q just released while chunk q+1 is already in
-// flight.  The stream of chunks runs straight through the reductions, so
-// the next pass's blocks arrive while the scalars are being formed.
-// lambda stays in global memory (one read-modify-write per iteration).
+// Tiled CTA-per-instance PCG (batched throughput form, opts.mode = 3).
+// One CTA owns an instance: r, p and a work vector w (S p, then Phi^-1 r)
+// live in shared memory for every knot, lambda in global memory.  The
+// CTA's lanes form knot streams of LPK lanes (two streams per warp when
+// LPK = 16); stream s owns a contiguous range of knots and walks it once per
+// pass (a pass is one product with S+ or with Phi^-1).  A step of a stream
+// consumes the tiles of one knot k: the diagonal block D_k and the
+// off-diagonal block O_k = block (k+1, k), which serves as the upper block of
+// row k (read by columns) and, one step later, as the lower block of row k+1
+// (read by rows), so each block crosses HBM once per pass.  The tiles
+// arrive by TMA bulk copies that complete on the stream's own mbarriers;
+// the copies for step g+1 are issued when step g starts, across pass
+// boundaries, so a stream's memory traffic keeps flowing while the CTA forms
+// the scalars.  Only the first knot of a range reads its lower block from
+// global memory directly (once per pass).  The diagonal blocks are exactly
+// symmetric, so reading row i of D_k gives the same products, in the same
+// order, as reading its column i.
 // ---------------------------------------------------------------------------
+// Per knot stream and pipeline depth d: a ring of d+1 diagonal-block tiles,
+// d+2 off-diagonal tiles and d+1 mbarriers.
+__host__ __device__ constexpr int tile_slots(int depth) { return 2 * depth + 3; }
+
 template <typename T>
-struct StreamLayout {
-    size_t r, p, rt, up, stage, stage_bytes, mbar, wpart, misc, total;
-    __host__ __device__ StreamLayout(int nmax, int vs, int W, int nx, int KC) {
+struct TileLayout {
+    size_t r, p, w, tiles, tile_bytes, stream_bytes, mbar, wpart, misc, total;
+    __host__ __device__ TileLayout(int nmax, int vs, int W, int NS, int nx, int depth) {
         using A = typename std::conditional<sizeof(T) == 4, dfloat, double>::type;
-        size_t o = 0;
         auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
+        size_t o = 0;
         const size_t v = sizeof(T) * (size_t)(nmax + 2) * vs;
         r = o; o = al(o + v);
         p = o; o = al(o + v);
-        rt = o; o = al(o + v);
-        up = o; o = al(o + v);
-        stage_bytes = al(sizeof(T) * (size_t)(2 * KC + 1) * nx * nx);
-        stage = o; o = o + 2 * stage_bytes;
-        mbar = o; o = al(o + 2 * sizeof(uint64_t));
+        w = o; o = al(o + v);
+        tile_bytes = (sizeof(T) * (size_t)nx * nx + 15) & ~size_t(15);
+        stream_bytes = (size_t)tile_slots(depth) * tile_bytes;
+        tiles = o; o = al(o + (size_t)NS * stream_bytes);
+        mbar = o; o = al(o + (size_t)NS * (depth + 1) * sizeof(uint64_t));
         wpart = o; o = al(o + 2 * sizeof(A) * W);
         misc = o; o = al(o + 16);
         total = o;
     }
 };
 
-template <typename T, int LPK, int RPT>
-__global__ void __launch_bounds__(256, 1) pcg_stream_kernel(const PcgParams<T> P) {
+template <typename T, int VW> struct VecT;
+template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<float, 2> { using type = float2; };
+template <> struct VecT<double, 2> { using type = double2; };
+
+// VW consecutive elements from 16- (or 8-) byte aligned shared memory
+template <typename T, int VW>
+__device__ __forceinline__ void vload(const T *p, T (&o)[VW]) {
+    const typename VecT<T, VW>::type v = *reinterpret_cast<const typename VecT<T, VW>::type *>(p);
+    if constexpr (VW == 4) {
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    } else {
+        o[0] = v.x; o[1] = v.y;
+    }
+}
+
+// Rows li, li + LPK, ... (RPT of them; rows >= nx skipped) of one block row
+// of the tiles times the halo'd vector: D (by rows), the lower block from a
+// tile (Lt, by rows; nullptr: none or Lg), the upper block U (by columns;
+// nullptr: none).  One pass over the columns feeds all three accumulators,
+// so the three dependency chains overlap; each accumulator still adds its
+// products in column order, as rowdot_ptr does.  nx % VW == 0.
+template <typename T, int VW, int RPT, int LPK>
+__device__ __forceinline__ void tile_rows(int nx, int li, const T *D, const T *Lt, const T *Lg,
+                                          const T *U, const T *vprev, const T *vself,
+                                          const T *vnext, T (&y)[RPT]) {
+    T a0[RPT], a1[RPT], a2[RPT];
+    bool ok[RPT];
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+        a0[m] = a1[m] = a2[m] = T(0);
+        ok[m] = li + m * LPK < nx;
+    }
+    // a missing block reads a zero row (its slot is never used for data)
+    const bool hasL = Lt != nullptr, hasU = U != nullptr;
+#pragma unroll 2
+    for (int j = 0; j < nx; j += VW) {
+        T xs[VW], xp[VW], xn[VW];
+        vload<T, VW>(vself + j, xs);
+        vload<T, VW>(vprev + j, xp);
+        vload<T, VW>(vnext + j, xn);
+#pragma unroll
+        for (int m = 0; m < RPT; ++m)
+            if (ok[m]) {
+                const int i = li + m * LPK;
+                T d[VW], l[VW];
+                vload<T, VW>(D + i * nx + j, d);
+                if (hasL) vload<T, VW>(Lt + i * nx + j, l);
+#pragma unroll
+                for (int t = 0; t < VW; ++t) {
+                    a0[m] = fma_rn(d[t], xs[t], a0[m]);
+                    if (hasL) a1[m] = fma_rn(l[t], xp[t], a1[m]);
+                    if (hasU) a2[m] = fma_rn(U[(j + t) * nx + i], xn[t], a2[m]);
+                }
+            }
+    }
+    if (Lg) {  // lower block of a stream's first knot, straight from global memory
+#pragma unroll
+        for (int m = 0; m < RPT; ++m)
+            if (ok[m])
+                for (int j = 0; j < nx; ++j)
+                    a1[m] = fma_rn(__ldg(Lg + (li + m * LPK) * nx + j), vprev[j], a1[m]);
+    }
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) y[m] = (a0[m] + a1[m]) + a2[m];
+}
+
+// b_i - (row i) . v with exact products and an extended sum (as resid_ptr)
+template <typename T>
+__device__ __forceinline__ T tile_resid(int nx, int i, T b, const T *D, const T *Lt, const T *Lg,
+                                        const T *U, const T *vprev, const T *vself,
+                                        const T *vnext) {
+    using AT = Acc<T>;
+    typename AT::type a = AT::prod(b, T(1));
+    for (int j = 0; j < nx; ++j) a = AT::add(a, AT::prod(-D[i * nx + j], vself[j]));
+    if (Lt)
+        for (int j = 0; j < nx; ++j) a = AT::add(a, AT::prod(-Lt[i * nx + j], vprev[j]));
+    else if (Lg)
+        for (int j = 0; j < nx; ++j) a = AT::add(a, AT::prod(-__ldg(Lg + i * nx + j), vprev[j]));
+    if (U)
+        for (int j = 0; j < nx; ++j) a = AT::add(a, AT::prod(-U[j * nx + i], vnext[j]));
+    return AT::to_T(a);
+}
+
+template <typename T, int LPK, int RPT, int VW>
+__global__ void __launch_bounds__(512, 1) pcg_tile_kernel(const PcgParams<T> P) {
     using AT = Acc<T>;
     using A = typename AT::type;
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int SW = 32 / LPK;  // streams per warp
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int W = nthreads / 32;
     const int warp = tid / 32, lane = tid % 32;
-    const int kl = tid / LPK, li = tid % LPK;
-    const int KC = nthreads / LPK;  // knots per chunk
-    const int nx = P.nx, vs = P.vs;
-    const int nx2 = nx * nx;
-    StreamLayout<T> Lo(P.kpc_max, vs, W, nx, KC);
+    const int NS = W * SW;
+    const int s = warp * SW + lane / LPK;  // this lane's stream
+    const int li = lane % LPK;
+    const bool leader = li == 0;
+    const int nx = P.nx, vs = P.vs, nx2 = nx * nx;
+    const uint32_t nxb = (uint32_t)(nx2 * sizeof(T));
+    const int depth = P.depth;       // steps copied ahead
+    const int RD = depth + 1, RO = depth + 2, RM = depth + 1;  // ring sizes
+    TileLayout<T> Lo(P.kpc_max, vs, W, NS, nx, depth);
     T *vr = reinterpret_cast<T *>(smem + Lo.r);
     T *vp = reinterpret_cast<T *>(smem + Lo.p);
-    T *vrt = reinterpret_cast<T *>(smem + Lo.rt);
-    T *vup = reinterpret_cast<T *>(smem + Lo.up);
-    unsigned char *stage0 = smem + Lo.stage;
+    T *vw = reinterpret_cast<T *>(smem + Lo.w);
+    unsigned char *tb = smem + Lo.tiles + (size_t)s * Lo.stream_bytes;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Lo.mbar);
     A *wpart = reinterpret_cast<A *>(smem + Lo.wpart);
-    int *s_misc = reinterpret_cast<int *>(smem + Lo.misc);  // [0] instance, [1] wait failure
+    int *s_misc = reinterpret_cast<int *>(smem + Lo.misc);
+    const uint32_t mbs = smem_u32(&mbar[(size_t)s * RM]);  // this stream's barriers
 
-    if (tid == 0) {
-        mbar_init(smem_u32(&mbar[0]), 1);
-        mbar_init(smem_u32(&mbar[1]), 1);
-        fence_mbar_init();
-    }
+    for (int e = tid; e < NS * RM; e += nthreads) mbar_init(smem_u32(&mbar[e]), 1);
+    if (tid == 0) fence_mbar_init();
     __syncthreads();
-    uint32_t ph[2] = {0u, 0u};  // next phase to wait for, per stage (tracked by every thread)
+    uint32_t ph = 0u;  // bit x: next phase parity of this stream's barrier x
 
     auto reduce2 = [&](A &x, A &y) {
 #pragma unroll
@@ -350,98 +448,116 @@ __global__ void __launch_bounds__(256, 1) pcg_stream_kernel(const PcgParams<T> P
         const int c0 = k0 - b;
         const bool bad = (P.info && P.info[b] != 0u) || Nb < 1 || Nb > P.kpc_max;
         const int max_iter = P.max_iter > 0 ? P.max_iter : 10 * Nb * nx;
-        const int nch = ceil_div(Nb, KC);
         int iters = 0, status = MPCG_CONVERGED;
         A eta = AT::zero(), bb = AT::zero();
         T rr_t = T(0);
 
-        // ---- the chunk stream: chunk q = pass q / nch, chunk q % nch; even
-        // passes read S+, odd passes Phi^-1 -------------------------------
-        auto issue = [&](int q) {  // thread 0 only
-            const int pass = q / nch, kb = (q % nch) * KC;
-            const T *Md = (pass & 1) ? P.Pd : P.Sd;
-            const T *Mo = (pass & 1) ? P.Po : P.So;
-            const int st = q & 1;
-            const uint32_t mb = smem_u32(&mbar[st]);
-            T *sD = reinterpret_cast<T *>(stage0 + st * Lo.stage_bytes);
-            T *sO = sD + (size_t)KC * nx2;
-            const int nd = min(KC, Nb - kb);
-            const int jlo = max(kb - 1, 0), jhi = min(kb + KC - 1, Nb - 2);
-            const uint32_t bd = (uint32_t)(nd * nx2 * sizeof(T));
-            const uint32_t bo = jhi >= jlo ? (uint32_t)((jhi - jlo + 1) * nx2 * sizeof(T)) : 0u;
-            mbar_arrive_expect(mb, bd + bo);
-            bulk_g2s(smem_u32(sD), Md + (size_t)(k0 + kb) * nx2, bd, mb);
-            if (bo) bulk_g2s(smem_u32(sO + (size_t)(jlo - (kb - 1)) * nx2), Mo + (size_t)(c0 + jlo) * nx2, bo, mb);
+        // this stream's knots [ks0, ks0 + len); every stream runs Lmax steps
+        // per pass so the two streams of a warp stay converged
+        const int ks0 = bad ? 0 : (int)(((long long)s * Nb) / NS);
+        const int len = bad ? 0 : (int)(((long long)(s + 1) * Nb) / NS) - ks0;
+        const int Lmax = bad ? 0 : ceil_div(Nb, NS);
+        // Pipeline state of this stream (identical in all its lanes).  Steps
+        // are numbered across passes; ring positions advance by one per step
+        // (no divisions in the loop).
+        int outstanding = 0;       // steps issued but not yet consumed
+        int i_t = 0, i_ps = 0;     // next step to issue: knot offset, pass
+        int i_d = 0, i_o = 0, i_m = 0;  // its D slot, O slot, barrier
+        int c_d = 0, c_o = 0, c_m = 0;  // next step to consume: D slot, O slot, barrier
+        int c_op = RO - 1;              // O slot of the step before it
+        auto wrap = [](int x, int n) { return x + 1 == n ? 0 : x + 1; };
+        auto tile = [&](int slot) { return reinterpret_cast<T *>(tb + (size_t)slot * Lo.tile_bytes); };
+        // the copies of the next step to issue (leader lane; len > 0): even
+        // passes read S+, odd passes Phi^-1
+        auto issue_next = [&]() {
+            const int k = ks0 + i_t;
+            const T *Md = (i_ps & 1) ? P.Pd : P.Sd;
+            const T *Mo = (i_ps & 1) ? P.Po : P.So;
+            const uint32_t bar = mbs + (uint32_t)(i_m * sizeof(uint64_t));
+            const bool hasU = k + 1 < Nb;
+            mbar_arrive_expect(bar, hasU ? 2u * nxb : nxb);
+            bulk_g2s(smem_u32(tile(i_d)), Md + (size_t)(k0 + k) * nx2, nxb, bar);
+            if (hasU) bulk_g2s(smem_u32(tile(RD + i_o)), Mo + (size_t)(c0 + k) * nx2, nxb, bar);
         };
-        int q = 0;  // next chunk to consume
-        int issued = 0;
-        auto wait_chunk = [&]() {
-            const int st = q & 1;
-            int fail = 0;
-            if (tid == 0) fail = !mbar_wait_bounded(smem_u32(&mbar[st]), ph[st], WAIT_LIMIT_NS);
-            ph[st] ^= 1u;
-            if (__syncthreads_or(fail)) failed = true;
-        };
-        auto release_chunk = [&]() {
-            __syncthreads();  // everyone is done reading stage q & 1
-            if (tid == 0) issue(issued);
-            ++issued;
-            ++q;
-        };
-        // one pass: y = M v for every knot (M = S+ or Phi^-1 by the pass
-        // parity); returns the thread's partial v . y (extended) and v . v
-        auto pass_apply = [&](const T *v, T *out, A &dot, T &sq) {
-            for (int c = 0; c < nch; ++c) {
-                wait_chunk();
-                if (failed) return;
-                const int st = (q & 1);
-                const T *sD = reinterpret_cast<const T *>(stage0 + st * Lo.stage_bytes);
-                const T *sO = sD + (size_t)KC * nx2;
-                const int k = c * KC + kl;
-                if (kl < KC && k < Nb) {
-                    const T *D = sD + (size_t)kl * nx2;
-                    const T *Lb = k >= 1 ? sO + (size_t)kl * nx2 : nullptr;
-                    const T *U = k + 1 < Nb ? sO + (size_t)(kl + 1) * nx2 : nullptr;
-#pragma unroll
-                    for (int m = 0; m < RPT; ++m) {
-                        const int i = li + m * LPK;
-                        if (i < nx) {
-                            const T y = rowdot_ptr<T>(nx, i, D, Lb, U, v + k * vs, v + (k + 1) * vs, v + (k + 2) * vs);
-                            out[(k + 1) * vs + i] = y;
-                            const T vi = v[(k + 1) * vs + i];
-                            dot = AT::add(dot, AT::prod(vi, y));
-                            sq = fma_rn(vi, vi, sq);
-                        }
-                    }
-                }
-                release_chunk();
+        auto advance_issue = [&]() {
+            if (++i_t == len) {
+                i_t = 0;
+                ++i_ps;
             }
+            i_d = wrap(i_d, RD);
+            i_o = wrap(i_o, RO);
+            i_m = wrap(i_m, RM);
+            ++outstanding;
         };
-        // residual pass: r = b - S lambda0 with extended sums (lambda0 in up)
-        auto pass_resid = [&](A &sbb) {
-            for (int c = 0; c < nch; ++c) {
-                wait_chunk();
-                if (failed) return;
-                const int st = (q & 1);
-                const T *sD = reinterpret_cast<const T *>(stage0 + st * Lo.stage_bytes);
-                const T *sO = sD + (size_t)KC * nx2;
-                const int k = c * KC + kl;
-                if (kl < KC && k < Nb) {
-                    const T *D = sD + (size_t)kl * nx2;
-                    const T *Lb = k >= 1 ? sO + (size_t)kl * nx2 : nullptr;
-                    const T *U = k + 1 < Nb ? sO + (size_t)(kl + 1) * nx2 : nullptr;
+        // wait for the next step's tiles (leader polls; warp-uniform result)
+        auto wait_next = [&](bool act) -> bool {
+            int f = 0;
+            if (act && leader)
+                f = !mbar_wait_bounded(mbs + (uint32_t)(c_m * sizeof(uint64_t)), (ph >> c_m) & 1u,
+                                       WAIT_LIMIT_NS);
+            if (act) ph ^= 1u << c_m;
+            return __any_sync(0xffffffffu, f) != 0;
+        };
+        auto advance_use = [&]() {
+            c_op = c_o;
+            c_d = wrap(c_d, RD);
+            c_o = wrap(c_o, RO);
+            c_m = wrap(c_m, RM);
+            --outstanding;
+        };
+        // one pass: kind 0 = residual out = b - S v (dot += b^2); kind 1 =
+        // product out = M v with partial dots (v . out, v . v)
+        auto run_pass = [&](int kind, int ps, const T *v, T *out, A &dot, T &sq) {
+            const T *Mo = (ps & 1) ? P.Po : P.So;
+            for (int t = 0; t < Lmax; ++t) {
+                const bool act = t < len;
+                __syncwarp();
+                if (act) {
+                    if (leader) {
+                        fence_proxy_async();  // generic reads of the slots precede the refill
+                        issue_next();
+                    }
+                    advance_issue();
+                }
+                if (wait_next(act)) {
+                    failed = true;
+                    break;
+                }
+                if (act) {
+                    const int k = ks0 + t;
+                    const T *D = tile(c_d);
+                    const T *U = k + 1 < Nb ? tile(RD + c_o) : nullptr;
+                    const T *Lt = (k >= 1 && t >= 1) ? tile(RD + c_op) : nullptr;
+                    const T *Lg = (k >= 1 && t == 0) ? Mo + (size_t)(c0 + k - 1) * nx2 : nullptr;
+                    advance_use();
+                    if (kind == 0) {
 #pragma unroll
-                    for (int m = 0; m < RPT; ++m) {
-                        const int i = li + m * LPK;
-                        if (i < nx) {
-                            const T bi = P.rhs_sign * P.rhs[(size_t)(k0 + k) * nx + i];
-                            vr[(k + 1) * vs + i] = resid_ptr<T>(nx, i, bi, D, Lb, U, vup + k * vs,
-                                                                vup + (k + 1) * vs, vup + (k + 2) * vs);
-                            sbb = AT::add(sbb, AT::prod(bi, bi));
+                        for (int m = 0; m < RPT; ++m) {
+                            const int i = li + m * LPK;
+                            if (i < nx) {
+                                const T bi = P.rhs_sign * P.rhs[(size_t)(k0 + k) * nx + i];
+                                out[(k + 1) * vs + i] = tile_resid<T>(nx, i, bi, D, Lt, Lg, U, v + k * vs,
+                                                                      v + (k + 1) * vs, v + (k + 2) * vs);
+                                dot = AT::add(dot, AT::prod(bi, bi));
+                            }
+                        }
+                    } else {
+                        T y[RPT];
+                        tile_rows<T, VW, RPT, LPK>(nx, li, D, Lt, Lg, U, v + k * vs, v + (k + 1) * vs,
+                                                   v + (k + 2) * vs, y);
+#pragma unroll
+                        for (int m = 0; m < RPT; ++m) {
+                            const int i = li + m * LPK;
+                            if (i < nx) {
+                                const int o = (k + 1) * vs + i;
+                                out[o] = y[m];
+                                const T vi = v[o];
+                                dot = AT::add(dot, AT::prod(vi, y[m]));
+                                sq = fma_rn(vi, vi, sq);
+                            }
                         }
                     }
                 }
-                release_chunk();
             }
         };
 
@@ -450,34 +566,36 @@ __global__ void __launch_bounds__(256, 1) pcg_stream_kernel(const PcgParams<T> P
         } else {
             const int nv = (Nb + 2) * vs;
             for (int e = tid; e < nv; e += nthreads) {
-                vr[e] = T(0); vp[e] = T(0); vrt[e] = T(0); vup[e] = T(0);
+                vr[e] = T(0); vp[e] = T(0); vw[e] = T(0);
             }
             __syncthreads();
-            for (int e = tid; e < Nb * nx; e += nthreads) {
+            for (int e = tid; e < Nb * nx; e += nthreads) {  // lambda0 into w (halo'd)
                 const int k = e / nx, i = e % nx;
-                vup[(k + 1) * vs + i] = P.lam[(size_t)(k0 + k) * nx + i];
+                vw[(k + 1) * vs + i] = P.lam[(size_t)(k0 + k) * nx + i];
             }
-            // prime the stream with the first two chunks
-            if (tid == 0) {
-                issue(0);
-                issue(1);
-            }
-            issued = 2;
+            // prime each stream's pipeline with its first `depth` steps
+            if (len > 0)
+                for (int g = 0; g < depth; ++g) {
+                    if (leader) issue_next();
+                    advance_issue();
+                }
             __syncthreads();
+            // pass 0: r = b - S lambda0 (extended), ||b||^2; pass 1: r~ = Phi^-1 r
             A sbb = AT::zero(), dummy = AT::zero();
-            pass_resid(sbb);
+            T sq0 = T(0);
+            run_pass(0, 0, vw, vr, sbb, sq0);
             reduce2(sbb, dummy);
             bb = sbb;
-            __syncthreads();
+            if (__syncthreads_or(failed)) failed = true;  // r complete, wpart read
             A s_eta = AT::zero();
             T sq = T(0);
-            if (!failed) pass_apply(vr, vrt, s_eta, sq);
+            if (!failed) run_pass(1, 1, vr, vw, s_eta, sq);
             A s_rr = AT::prod(sq, T(1));
             reduce2(s_eta, s_rr);
             eta = s_eta;
             rr_t = AT::to_T(s_rr);
-            __syncthreads();
-            for (int e = tid; e < nv; e += nthreads) vp[e] = vrt[e];
+            if (__syncthreads_or(failed)) failed = true;
+            for (int e = tid; e < nv; e += nthreads) vp[e] = vw[e];
             __syncthreads();
 
             const double tol = P.tol > 0 ? P.tol : 1e-6;
@@ -488,6 +606,7 @@ __global__ void __launch_bounds__(256, 1) pcg_stream_kernel(const PcgParams<T> P
                 return rr_ <= tol_rr;
             };
             T eta_t = AT::to_T(eta);
+            int ps = 2;
             if (failed) {
                 status = MPCG_TIMEOUT;
             } else if (!(isfinite(eta_t) && isfinite(rr_t))) {
@@ -497,10 +616,14 @@ __global__ void __launch_bounds__(256, 1) pcg_stream_kernel(const PcgParams<T> P
                 for (int it = 1; it <= max_iter; ++it) {
                     A s1 = AT::zero(), s1b = AT::zero();
                     T sq1 = T(0);
-                    pass_apply(vp, vup, s1, sq1);  // S p and p^T S p
+                    run_pass(1, ps++, vp, vw, s1, sq1);  // S p and p^T S p
                     reduce2(s1, s1b);
                     iters = it;
-                    if (failed) { status = MPCG_TIMEOUT; break; }
+                    if (__syncthreads_or(failed)) {
+                        failed = true;
+                        status = MPCG_TIMEOUT;
+                        break;
+                    }
                     const T ups = AT::to_T(s1);
                     if (!(ups > T(0)) || !isfinite(ups)) {
                         status = MPCG_BREAKDOWN;
@@ -512,15 +635,19 @@ __global__ void __launch_bounds__(256, 1) pcg_stream_kernel(const PcgParams<T> P
                         const int o = (k + 1) * vs + i;
                         T *lp = &P.lam[(size_t)(k0 + k) * nx + i];
                         *lp = fma_rn(alpha, vp[o], *lp);
-                        vr[o] = fma_rn(-alpha, vup[o], vr[o]);
+                        vr[o] = fma_rn(-alpha, vw[o], vr[o]);
                     }
                     __syncthreads();
                     A s2 = AT::zero();
                     T sq2 = T(0);
-                    pass_apply(vr, vrt, s2, sq2);  // r~ = Phi^-1 r, r^T r~, ||r||^2
+                    run_pass(1, ps++, vr, vw, s2, sq2);  // r~ = Phi^-1 r, r^T r~, ||r||^2
                     A s2b = AT::prod(sq2, T(1));
                     reduce2(s2, s2b);
-                    if (failed) { status = MPCG_TIMEOUT; break; }
+                    if (__syncthreads_or(failed)) {
+                        failed = true;
+                        status = MPCG_TIMEOUT;
+                        break;
+                    }
                     const T etan = AT::to_T(s2);
                     rr_t = AT::to_T(s2b);
                     eta = s2;
@@ -537,18 +664,22 @@ __global__ void __launch_bounds__(256, 1) pcg_stream_kernel(const PcgParams<T> P
                     for (int e = tid; e < Nb * nx; e += nthreads) {
                         const int k = e / nx, i = e % nx;
                         const int o = (k + 1) * vs + i;
-                        vp[o] = fma_rn(beta, vp[o], vrt[o]);
+                        vp[o] = fma_rn(beta, vp[o], vw[o]);
                     }
                     __syncthreads();
                 }
             }
-            // drain the copies still in flight (chunks q and q+1) before the
-            // stages are reused or the CTA leaves
-            for (int d = 0; d < 2 && !failed; ++d) {
-                wait_chunk();
-                ++q;
+            // drain this stream's copies still in flight (issued, not
+            // consumed) before the slots are reused or the CTA leaves; after
+            // a timed-out wait both barriers may still be pending
+            // (at most depth + 1; a warp-uniform trip count keeps both
+            // streams of a warp together)
+            for (int d = 0; d <= depth; ++d) {
+                const bool act = len > 0 && outstanding > 0;
+                if (wait_next(act)) failed = true;
+                if (act) advance_use();
             }
-            __syncthreads();
+            if (__syncthreads_or(failed)) failed = true;
         }
         if (tid == 0 && P.stats) {
             mpcg_stats st;
@@ -607,54 +738,65 @@ cudaError_t pcg_cta_prepare(int smem_optin) {
 }
 
 template <typename T>
-static void (*pcg_stream_fn(const PcgLaunch &L))(const PcgParams<T>) {
-    if (L.lpk == 16) return pcg_stream_kernel<T, 16, 1>;
-    if (L.rpt == 1) return pcg_stream_kernel<T, 32, 1>;
-    return pcg_stream_kernel<T, 32, 2>;
+static void (*pcg_tile_fn(const PcgLaunch &L))(const PcgParams<T>) {
+    if constexpr (sizeof(T) == 4) {
+        if (L.vw == 4) {
+            if (L.lpk == 16) return pcg_tile_kernel<T, 16, 1, 4>;
+            if (L.rpt == 1) return pcg_tile_kernel<T, 32, 1, 4>;
+            return pcg_tile_kernel<T, 32, 2, 4>;
+        }
+    }
+    if (L.lpk == 16) return pcg_tile_kernel<T, 16, 1, 2>;
+    if (L.rpt == 1) return pcg_tile_kernel<T, 32, 1, 2>;
+    return pcg_tile_kernel<T, 32, 2, 2>;
 }
 
 template <typename T>
-size_t pcg_stream_smem_bytes(int nmax, int vs, int W, int nx, int KC) {
-    return StreamLayout<T>(nmax, vs, W, nx, KC).total;
+size_t pcg_tile_smem_bytes(int nmax, int vs, int W, int NS, int nx, int depth) {
+    return TileLayout<T>(nmax, vs, W, NS, nx, depth).total;
 }
 
 template <typename T>
-cudaError_t pcg_stream_launch(const PcgLaunch &L, const PcgParams<T> &P0, cudaStream_t s) {
+cudaError_t pcg_tile_launch(const PcgLaunch &L, const PcgParams<T> &P0, cudaStream_t s) {
     PcgParams<T> P = P0;
-    P.kpc_max = L.kpc_max;
+    P.kpc_max = L.kpc_max;  // largest horizon: sizes the shared vectors
     P.stage_smem = 0;
     P.vs = L.vs;
-    pcg_stream_fn<T>(L)<<<L.clusters, L.threads, L.smem, s>>>(P);
+    P.depth = L.depth;
+    pcg_tile_fn<T>(L)<<<L.clusters, L.threads, L.smem, s>>>(P);
     return cudaGetLastError();
 }
 
 template <typename T>
-int pcg_stream_max_blocks(const PcgLaunch &L) {
+int pcg_tile_max_blocks(const PcgLaunch &L) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pcg_stream_fn<T>(L), L.threads, L.smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pcg_tile_fn<T>(L), L.threads, L.smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return n;
 }
 
-cudaError_t pcg_stream_prepare(int smem_optin) {
+cudaError_t pcg_tile_prepare(int smem_optin) {
     cudaError_t e;
     const auto a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if ((e = cudaFuncSetAttribute(pcg_stream_kernel<float, 16, 1>, a, smem_optin))) return e;
-    if ((e = cudaFuncSetAttribute(pcg_stream_kernel<float, 32, 1>, a, smem_optin))) return e;
-    if ((e = cudaFuncSetAttribute(pcg_stream_kernel<float, 32, 2>, a, smem_optin))) return e;
-    if ((e = cudaFuncSetAttribute(pcg_stream_kernel<double, 16, 1>, a, smem_optin))) return e;
-    if ((e = cudaFuncSetAttribute(pcg_stream_kernel<double, 32, 1>, a, smem_optin))) return e;
-    return cudaFuncSetAttribute(pcg_stream_kernel<double, 32, 2>, a, smem_optin);
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 16, 1, 4>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 1, 4>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 4>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 16, 1, 2>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 1, 2>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 2>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<double, 16, 1, 2>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<double, 32, 1, 2>, a, smem_optin))) return e;
+    return cudaFuncSetAttribute(pcg_tile_kernel<double, 32, 2, 2>, a, smem_optin);
 }
 
-template size_t pcg_stream_smem_bytes<float>(int, int, int, int, int);
-template size_t pcg_stream_smem_bytes<double>(int, int, int, int, int);
-template cudaError_t pcg_stream_launch<float>(const PcgLaunch &, const PcgParams<float> &, cudaStream_t);
-template cudaError_t pcg_stream_launch<double>(const PcgLaunch &, const PcgParams<double> &, cudaStream_t);
-template int pcg_stream_max_blocks<float>(const PcgLaunch &);
-template int pcg_stream_max_blocks<double>(const PcgLaunch &);
+template size_t pcg_tile_smem_bytes<float>(int, int, int, int, int, int);
+template size_t pcg_tile_smem_bytes<double>(int, int, int, int, int, int);
+template cudaError_t pcg_tile_launch<float>(const PcgLaunch &, const PcgParams<float> &, cudaStream_t);
+template cudaError_t pcg_tile_launch<double>(const PcgLaunch &, const PcgParams<double> &, cudaStream_t);
+template int pcg_tile_max_blocks<float>(const PcgLaunch &);
+template int pcg_tile_max_blocks<double>(const PcgLaunch &);
 template size_t pcg_cta_smem_bytes<float>(int, int, int);
 template size_t pcg_cta_smem_bytes<double>(int, int, int);
 template cudaError_t pcg_cta_launch<float>(const PcgLaunch &, const PcgParams<float> &, cudaStream_t);

@@ -152,10 +152,13 @@ def test_paper_exit_mode():
                                            (14, 7, 17, "float32"), (14, 7, 33, "float32"),
                                            (14, 7, 256, "float32"), (14, 7, 512, "float32"),
                                            (2, 1, 9, "float32"), (4, 2, 47, "float32"),
-                                           (36, 12, 40, "float32"), (14, 7, 200, "float64")])
+                                           (36, 12, 40, "float32"), (14, 7, 200, "float64"),
+                                           (36, 12, 256, "float32"), (36, 12, 64, "float64"),
+                                           (20, 8, 77, "float32"), (6, 3, 50, "float32")])
 def test_cta_mode_parity(nx, nu, N, dtype, mode):
-    """One CTA per instance: L2 reads (mode 2) and TMA-staged blocks (mode 3);
-    N = 17 and 33 leave ragged last chunks of the 16-knot stream."""
+    """One CTA per instance: L2 reads (mode 2) and TMA tiles (mode 3).  Shapes cover one and two streams per warp, one
+    and two rows per lane, 2- and 4-wide row loads, horizons shorter than
+    the stream count and ragged stream ranges."""
     from paper_2309_08079_gb300.solver import make_opts
     lq = gen.kuka_lq(nx, nu, N, 600 + N + nx)
     tol = TOL_F32 if dtype == "float32" else TOL_F64
