@@ -359,10 +359,11 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": "pcg_cluster_kernel", "peak_source": peak_note,
                 "alg_bytes_per_launch": alg_bytes, "launch_us": pcg_s * 1e6}
 
-    batched = backward = sweep = exit_sweep = large = None
+    batched = backward = sweep = exit_sweep = precon_compare = large = None
     if not args.no_sweep:
         sweep = run_sweep(s, dev, args.sweep_reps, flush)
         exit_sweep = run_exit_sweep(s, dev, min(args.sweep_reps, 200))
+        precon_compare = run_precon_compare(s, dev, min(args.sweep_reps, 100))
     if not args.no_batched:
         batched = run_batched(s, dev, args.batched_solves)
         backward = run_backward(s, dev)
@@ -403,7 +404,7 @@ def run_ours(args, rank, world, local_rank):
         "parity": {"err_lambda": err_lam, "err_dz": err_dz, "tol": 1e-4},
         "clocks": clk, "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roofline,
         "cpu_baseline": cpu, "batched": batched, "backward": backward, "sweep": sweep,
-        "exit_sweep": exit_sweep, "large_state": large,
+        "exit_sweep": exit_sweep, "precon_compare": precon_compare, "large_state": large,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -753,6 +754,46 @@ def run_exit_sweep(s, dev, reps):
                      "err_lambda_vs_oracle": pct(errs)}
     return {"workload": f"single instance N={N}, nx={c['nx']}, {reps} warm-started PCG solves per exit test",
             "per_exit": out}
+
+
+def run_precon_compare(s, dev, reps):
+    """The symmetric stair preconditioner of Sec. IV-A against block Jacobi
+    (Phi^-1 = D^-1) on the sweep instances N = 128 and 512: warm-started PCG
+    iterations and time, and the error each leaves against the oracle."""
+    import torch
+    import oracle
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    c = gen.CONFIG_SWEEP
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for N in (128, 512):
+        lq = gen.kuka_lq(c["nx"], c["nu"], N, c["seed_base"] + N, dt=c["dt"], qd=c["qd"]).astype(np.float32)
+        lo, _, _ = oracle.kkt_solve(lq.astype(np.float64))
+        lt = LQTensors.from_numpy(lq, device=dev)
+        sch = s.alloc_schur(lt)
+        lam_star, _, _, _, _ = s.solve(lt, opts=make_opts(), schur=sch)
+        ls = lam_star.cpu().double().numpy()
+        lams0 = torch.as_tensor(np.stack([gen.warm_start(ls, c["seed_base"] + N, r) for r in range(reps)]),
+                                dtype=torch.float32, device=dev)
+        for name, pc in (("symmetric_stair", 0), ("block_jacobi", 1)):
+            o = make_opts(tol=1e-6, precon=pc)
+            cold = s.alloc_stats(1, dev)
+            s.pcg_solve(lt, sch, torch.zeros_like(lams0[0]), o, cold)
+            lams = lams0.clone()
+            stats = s.alloc_stats(reps, dev)
+            s.pcg_solve(lt, sch, lams0[0].clone(), o)
+            torch.cuda.synchronize()
+            tim = _step_timer(s, stream)
+            for r in range(reps):
+                tim(lambda: s.pcg_solve(lt, sch, lams[r], o, stats[r * 24:(r + 1) * 24]))
+            torch.cuda.synchronize()
+            st = read_stats(stats)
+            out[f"N{N}_{name}"] = {"pcg_us": pct(np.array(tim.ms()) * 1e3), "iters": pct(st["iters"]),
+                                   "cold_iters": int(read_stats(cold)["iters"][0]),
+                                   "converged": bool(np.all(st["status"] == 0)),
+                                   "err_lambda_vs_oracle": oracle.relerr(lams[reps - 1].cpu().double().numpy(), lo)}
+    return {"workload": f"single instances N in (128, 512), nx={c['nx']}, {reps} warm-started PCG solves "
+                        f"per preconditioner, rel. residual 1e-6", "per_case": out}
 
 
 def run_large(s, dev, solves, B=None):

@@ -108,6 +108,10 @@ typedef struct {
        listed instances, which sizes the launch. */
     const int *instances;
     int n_instances;
+    /* Preconditioner applied by the PCG: 0 the symmetric stair Phi^-1 of
+       Sec. IV-A (Pd and Po, the default); 1 block Jacobi, Phi^-1 = D^-1 (Pd
+       only; Po is not read), for comparison.  Other values: MPCG_EINVAL. */
+    int precon;
 } mpcg_opts;
 
 typedef struct {

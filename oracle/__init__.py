@@ -6,7 +6,7 @@ CPU-baseline leg may import it.  It shares no code with the CUDA path; both
 take their inputs from ``workload``.
 """
 from .oracle import (  # noqa: F401
-    build, kkt_solve, kkt_solve_rhs, kkt_dim, schur_blocks, precon_blocks,
+    build, kkt_solve, kkt_solve_rhs, kkt_dim, schur_blocks, precon_blocks, jacobi_blocks,
     dense_S, dense_Phi_inv, block_tridiag_sparse, pcg, recover, grad, loss,
     solve_batch, natural_z, split_z, relerr,
 )

@@ -197,6 +197,13 @@ def precon_blocks(Sd: np.ndarray, So: np.ndarray):
     return Pd, Po
 
 
+def jacobi_blocks(Sd: np.ndarray, So: np.ndarray):
+    """Block-Jacobi preconditioner Phi^-1 = D^-1 (the block diagonal of S+
+    inverted; no off-diagonal blocks): the comparison baseline for the
+    symmetric stair preconditioner of Sec. IV-A."""
+    return np.linalg.inv(Sd), np.zeros_like(So)
+
+
 def block_tridiag_sparse(Dd: np.ndarray, Do: np.ndarray) -> sp.csr_matrix:
     """Assemble a symmetric block-tridiagonal matrix from Dd and Do (below)."""
     N, nx, _ = Dd.shape

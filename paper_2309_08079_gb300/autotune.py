@@ -132,7 +132,7 @@ class PlanRunner:
         for j, (g, idx) in enumerate(groups):
             inst = torch.as_tensor(idx.astype(np.int32), device=lq.device)
             o = make_opts(tol=b.tol, tol_mode=b.tol_mode, max_iter=b.max_iter,
-                          cluster=g["cluster"], mode=g["mode"], instances=inst)
+                          cluster=g["cluster"], mode=g["mode"], instances=inst, precon=b.precon)
             self.launches.append(_Launch(o, int(Ns[idx].max()), inst,
                                          self.ws[QUEUE_BYTES * j:QUEUE_BYTES * (j + 1)]))
         self.streams = [torch.cuda.Stream(lq.device) for _ in self.launches[1:]]

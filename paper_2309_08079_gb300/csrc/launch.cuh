@@ -33,6 +33,7 @@ struct PcgParams {
     double tol;
     int tol_mode;
     int max_iter;     // <= 0: 10 N nx
+    int precon;       // 0: symmetric stair Phi^-1 (Pd, Po); 1: block Jacobi (Pd only)
     int kpc_max;      // knot slots per CTA (blockDim.x / LPK)
     int stage_smem;   // PTR mode: stage blocks in shared memory
     int vs;           // shared vector stride (elements per knot)

@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
         const T *pPd = nullptr, *pPl = nullptr, *pPu = nullptr;
         const int nx2 = nx * nx;
 
+        const bool jac = P.precon == 1;
         if (!bad) {
             if constexpr (MODE == MODE_REG) {
                 const bool hl = active_knot && k >= 1, hu = active_knot && k + 1 < Nb;
@@ -286,9 +287,9 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
                         sd[m][j] = v ? __ldg(Sd + j * NXR + i) : 0.f;
                         qd[m][j] = v ? __ldg(Pd + j * NXR + i) : 0.f;
                         sl[m][j] = (v && hl) ? __ldg(SoL + i * NXR + j) : 0.f;
-                        ql[m][j] = (v && hl) ? __ldg(PoL + i * NXR + j) : 0.f;
+                        ql[m][j] = (v && hl && !jac) ? __ldg(PoL + i * NXR + j) : 0.f;
                         su[m][j] = (v && hu) ? __ldg(SoU + j * NXR + i) : 0.f;
-                        qu[m][j] = (v && hu) ? __ldg(PoU + j * NXR + i) : 0.f;
+                        qu[m][j] = (v && hu && !jac) ? __ldg(PoU + j * NXR + i) : 0.f;
                     }
                 }
             } else {
@@ -331,6 +332,7 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
                     if (k >= 1) { pSl = P.So + (size_t)(c0 + k - 1) * nx2; pPl = P.Po + (size_t)(c0 + k - 1) * nx2; }
                     if (k + 1 < Nb) { pSu = P.So + (size_t)(c0 + k) * nx2; pPu = P.Po + (size_t)(c0 + k) * nx2; }
                 }
+                if (jac) pPl = pPu = nullptr;  // block Jacobi: Phi^-1 = D^-1
             }
         }
 

@@ -101,9 +101,10 @@ __global__ void __launch_bounds__(512, 1) pcg_cta_kernel(const PcgParams<T> P) {
         auto blocks = [&](int k, bool precon, const T *&D, const T *&Lo, const T *&U) {
             const T *Md = precon ? P.Pd : P.Sd;
             const T *Mo = precon ? P.Po : P.So;
+            const bool off = !(precon && P.precon == 1);  // block Jacobi: Phi^-1 = D^-1
             D = Md + (size_t)(k0 + k) * nx2;
-            Lo = k >= 1 ? Mo + (size_t)(c0 + k - 1) * nx2 : nullptr;
-            U = k + 1 < Nb ? Mo + (size_t)(c0 + k) * nx2 : nullptr;
+            Lo = (off && k >= 1) ? Mo + (size_t)(c0 + k - 1) * nx2 : nullptr;
+            U = (off && k + 1 < Nb) ? Mo + (size_t)(c0 + k) * nx2 : nullptr;
         };
         // y = M v over all knots into out; returns the thread's partial dots
         // (v . y, v . v) accumulated in extended precision / plain T.
@@ -474,7 +475,8 @@ __global__ void __launch_bounds__(512, 1) pcg_tile_kernel(const PcgParams<T> P) 
             const T *Md = (i_ps & 1) ? P.Pd : P.Sd;
             const T *Mo = (i_ps & 1) ? P.Po : P.So;
             const uint32_t bar = mbs + (uint32_t)(i_m * sizeof(uint64_t));
-            const bool hasU = k + 1 < Nb;
+            // block Jacobi passes (odd, Phi^-1) use no off-diagonal blocks
+            const bool hasU = k + 1 < Nb && !((i_ps & 1) && P.precon == 1);
             mbar_arrive_expect(bar, hasU ? 2u * nxb : nxb);
             bulk_g2s(smem_u32(tile(i_d)), Md + (size_t)(k0 + k) * nx2, nxb, bar);
             if (hasU) bulk_g2s(smem_u32(tile(RD + i_o)), Mo + (size_t)(c0 + k) * nx2, nxb, bar);
@@ -525,10 +527,11 @@ __global__ void __launch_bounds__(512, 1) pcg_tile_kernel(const PcgParams<T> P) 
                 }
                 if (act) {
                     const int k = ks0 + t;
+                    const bool off = !((ps & 1) && P.precon == 1);
                     const T *D = tile(c_d);
-                    const T *U = k + 1 < Nb ? tile(RD + c_o) : nullptr;
-                    const T *Lt = (k >= 1 && t >= 1) ? tile(RD + c_op) : nullptr;
-                    const T *Lg = (k >= 1 && t == 0) ? Mo + (size_t)(c0 + k - 1) * nx2 : nullptr;
+                    const T *U = (off && k + 1 < Nb) ? tile(RD + c_o) : nullptr;
+                    const T *Lt = (off && k >= 1 && t >= 1) ? tile(RD + c_op) : nullptr;
+                    const T *Lg = (off && k >= 1 && t == 0) ? Mo + (size_t)(c0 + k - 1) * nx2 : nullptr;
                     advance_use();
                     if (kind == 0) {
 #pragma unroll

@@ -102,11 +102,14 @@ class SchurTensors:
                                                       self.gamma, self.info)))
 
 
-def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0, mode=0, instances=None) -> L.mpcg_opts:
+def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0, mode=0, instances=None,
+              precon=0) -> L.mpcg_opts:
     """mode: 0 automatic, 1 cluster per instance, 2 one CTA per instance
-    reading blocks from L2, 3 one CTA per instance with TMA-staged blocks
-    (as 2 when blocks are not 16-byte multiples)."""
-    o = L.mpcg_opts(float(tol), int(tol_mode), int(max_iter), int(cluster), int(mode), None, 0)
+    reading blocks from L2, 3 one CTA per instance streaming TMA tiles (as 2
+    when blocks are not 16-byte multiples).  precon: 0 symmetric stair
+    (Sec. IV-A), 1 block Jacobi."""
+    o = L.mpcg_opts(float(tol), int(tol_mode), int(max_iter), int(cluster), int(mode), None, 0,
+                    int(precon))
     if instances is not None:  # a device int32 tensor of instance indices
         o.instances = instances.data_ptr()
         o.n_instances = int(instances.numel())

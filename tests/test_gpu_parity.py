@@ -213,3 +213,32 @@ def test_status_nonfinite():
     lq.A[4, 1, 1] = np.nan
     _, _, _, st, _ = run_gpu(lq.astype(np.float32))
     assert st["status"][0] in (2, 3)
+
+
+# ------------------------------------------------------------------ block-Jacobi comparison preconditioner
+@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("nx,nu,N,dtype", [(14, 7, 128, "float32"), (14, 7, 512, "float32"),
+                                           (36, 12, 64, "float32"), (14, 7, 100, "float64")])
+def test_block_jacobi_parity(nx, nu, N, dtype, mode):
+    """opts.precon = 1 (Phi^-1 = D^-1) in every kernel form: the same solution,
+    and about the iteration count of the oracle's Algorithm 1 with the same
+    preconditioner."""
+    from paper_2309_08079_gb300.solver import make_opts
+    f32 = dtype == "float32"
+    lq = gen.kuka_lq(nx, nu, N, 700 + N + nx)
+    tol = 1e-6 if f32 else 1e-13
+    e_lam, e_dz, st = parity(lq, dtype=dtype, opts=make_opts(mode=mode, precon=1, tol=tol))
+    assert st["status"][0] == 0, st
+    bar = TOL_F32 if f32 else TOL_F64
+    assert e_lam < bar and e_dz < bar, (e_lam, e_dz)
+    lq_in = lq.astype(np.float32 if f32 else np.float64).astype(np.float64)
+    Sd, So, g = oracle.schur_blocks(lq_in)
+    _, it_o, ok = oracle.pcg(Sd, So, *oracle.jacobi_blocks(Sd, So), -g, tol=tol)
+    assert ok and abs(int(st["iters"][0]) - it_o) <= max(3, 0.1 * it_o), (st["iters"][0], it_o)
+
+
+def test_precon_value_is_checked():
+    from paper_2309_08079_gb300.solver import make_opts
+    from paper_2309_08079_gb300._lib import MPCGError
+    with pytest.raises(MPCGError):
+        run_gpu(gen.kuka_lq(14, 7, 16, 1).astype(np.float32), opts=make_opts(precon=2))

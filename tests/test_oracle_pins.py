@@ -276,3 +276,50 @@ def test_grad_vs_central_differences():
             fd = (L(p) - L(m)) / (2 * h)
             an = g[name][idx]
             assert abs(fd - an) <= 1e-7 * max(1.0, abs(an)) + round_err, (name, idx, fd, an)
+
+
+# ---------------------------------------------------------------- block-Jacobi comparison preconditioner
+def test_jacobi_blocks_invert_the_block_diagonal():
+    lq = gen.kuka_lq(14, 7, 20, 31)
+    Sd, So, _ = oracle.schur_blocks(lq)
+    Jd, Jo = oracle.jacobi_blocks(Sd, So)
+    assert np.all(Jo == 0.0)
+    eye = np.broadcast_to(np.eye(14), Sd.shape)
+    assert np.abs(np.einsum("kij,kjl->kil", Jd, Sd) - eye).max() < 1e-10
+
+
+def test_jacobi_pcg_matches_scipy_preconditioned_cg():
+    """Algorithm 1 with Phi^-1 = D^-1 against scipy's CG given the same
+    preconditioner as a LinearOperator (an independent PCG)."""
+    import scipy.sparse.linalg as spla
+    lq = gen.kuka_lq(4, 2, 12, 19)
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    Jd, Jo = oracle.jacobi_blocks(Sd, So)
+    lam_p, it, ok = oracle.pcg(Sd, So, Jd, Jo, -gamma, tol=1e-11)
+    S = oracle.block_tridiag_sparse(Sd, So)
+    Dinv = np.linalg.inv(Sd)
+    M = spla.LinearOperator(S.shape, matvec=lambda v: np.einsum("kij,kj->ki", Dinv, v.reshape(Sd.shape[:2])).ravel())
+    x, info = spla.cg(S, -gamma.ravel(), M=M, rtol=1e-13, maxiter=10000)
+    assert ok and info == 0 and oracle.relerr(lam_p, x) < 1e-8
+
+
+def test_jacobi_decoupled_converges_in_one_iteration():
+    lq = gen.kuka_lq(6, 3, 10, 23)
+    lq.A[:] = 0.0
+    lq.B[:] = 0.0
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    Jd, Jo = oracle.jacobi_blocks(Sd, So)
+    lam_p, it, ok = oracle.pcg(Sd, So, Jd, Jo, -gamma, tol=1e-12)
+    lam, _, _ = oracle.kkt_solve(lq)
+    assert ok and it == 1 and oracle.relerr(lam_p, lam) < 1e-13
+
+
+def test_symmetric_stair_needs_fewer_iterations_than_block_jacobi():
+    """The reason Sec. IV-A adds the off-diagonal blocks: on the Kuka-shaped
+    workload the symmetric stair preconditioner roughly halves the PCG
+    iterations of block Jacobi."""
+    lq = gen.kuka_lq(14, 7, 128, 130)
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    _, it_s, ok_s = oracle.pcg(Sd, So, *oracle.precon_blocks(Sd, So), -gamma, tol=1e-6)
+    _, it_j, ok_j = oracle.pcg(Sd, So, *oracle.jacobi_blocks(Sd, So), -gamma, tol=1e-6)
+    assert ok_s and ok_j and it_s < 0.7 * it_j, (it_s, it_j)
