@@ -75,6 +75,12 @@ def candidate_plans(Ns: np.ndarray) -> Dict[str, List[dict]]:
         plans["classes_cta_short"] = short + [
             {"lo": max(a, cut) if short else a, "hi": b, "mode": 0, "cluster": 0}
             for a, b in zip(lo, edges) if b > cut]
+        # per-class launches of the CTA-per-instance kernels (each class's
+        # shared vectors sized for its own longest horizon)
+        plans["classes_cta_l2"] = [{"lo": a, "hi": b, "mode": 2, "cluster": 0}
+                                   for a, b in zip(lo, edges)]
+        plans["classes_tile"] = [{"lo": a, "hi": b, "mode": 3, "cluster": 0}
+                                 for a, b in zip(lo, edges)]
         # finer knots-per-CTA tiling: clusters of ceil(hi / kpc) CTAs holding
         # kpc knots each, so a smaller CTA shares its SM with another
         # instance's CTA (classes whose cluster would exceed 16 keep the
