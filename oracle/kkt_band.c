@@ -9,7 +9,8 @@
  *      [ G  C^T ] [ y_z ]   [ h_z ]
  *      [ C   0  ] [ y_l ] = [ h_l ]
  *
- * with G = diag(Q_0, R_0, Q_1, R_1, ..., Q_{N-1}) (diagonal Q_k, R_k) and C
+ * with G = diag(Q_0, R_0, Q_1, R_1, ..., Q_{N-1}) (diagonal Q_k, R_k, or
+ * dense SPD blocks when given) and C
  * the dynamics Jacobian: block row 0 is [I 0 ...]; block row k+1 holds
  * -A_k, -B_k, I on the columns of x_k, u_k, x_{k+1}.  For the forward solve
  * the right-hand side is (g, c) and the unknown is (-dz, lambda); the same
@@ -57,7 +58,7 @@ static void band_set(band_t *m, long i, long j, double v) { *band_at(m, i, j) = 
  * hold the stationarity rows [G C^T].
  */
 static void assemble(band_t *m, int nx, int nu, int N, const double *A, const double *B,
-                     const double *Qd, const double *Rd) {
+                     const double *Qd, const double *Rd, const double *Q, const double *R) {
     for (int k = 0; k < N; ++k) {
         long bl = knot_base(k, nx, nu), bx = bl + nx, bu = bl + 2 * nx;
         /* constraint row k: I on x_k, and -A_{k-1}, -B_{k-1} on x_{k-1}, u_{k-1} */
@@ -73,7 +74,10 @@ static void assemble(band_t *m, int nx, int nu, int N, const double *A, const do
         }
         /* stationarity of x_k: Q_k on x_k, I on lam_k, -A_k^T on lam_{k+1} */
         for (int i = 0; i < nx; ++i) {
-            band_set(m, bx + i, bx + i, Qd[(long)k * nx + i]);
+            if (Q)
+                for (int j = 0; j < nx; ++j) band_set(m, bx + i, bx + j, Q[((long)k * nx + i) * nx + j]);
+            else
+                band_set(m, bx + i, bx + i, Qd[(long)k * nx + i]);
             band_set(m, bx + i, bl + i, 1.0);
             if (k < N - 1) {
                 long nb = knot_base(k + 1, nx, nu);
@@ -86,7 +90,10 @@ static void assemble(band_t *m, int nx, int nu, int N, const double *A, const do
             long nb = knot_base(k + 1, nx, nu);
             const double *Bk = B + (long)k * nx * nu;
             for (int i = 0; i < nu; ++i) {
-                band_set(m, bu + i, bu + i, Rd[(long)k * nu + i]);
+                if (R)
+                    for (int j = 0; j < nu; ++j) band_set(m, bu + i, bu + j, R[((long)k * nu + i) * nu + j]);
+                else
+                    band_set(m, bu + i, bu + i, Rd[(long)k * nu + i]);
                 for (int j = 0; j < nx; ++j) band_set(m, bu + i, nb + j, -Bk[j * nu + i]);
             }
         }
@@ -140,12 +147,15 @@ long oracle_kkt_dim(int nx, int nu, int N) {
 
 /*
  * Solve K y = h.  h and y are in natural order: z-part (N nx + (N-1) nu
- * entries) followed by the lambda-part (N nx).  y may alias h.
+ * entries) followed by the lambda-part (N nx).  y may alias h.  Q and R,
+ * when not NULL, are dense cost blocks Q[N][nx][nx], R[N-1][nu][nu] used
+ * instead of the diagonals Qd, Rd.
  * Returns 0 on success, 1 if singular, 2 on bad arguments, 3 on allocation
  * failure.
  */
-int oracle_kkt_solve(int nx, int nu, int N, const double *A, const double *B,
-                     const double *Qd, const double *Rd, const double *h, double *y) {
+int oracle_kkt_solve_g(int nx, int nu, int N, const double *A, const double *B,
+                       const double *Qd, const double *Rd, const double *Q, const double *R,
+                       const double *h, double *y) {
     if (nx <= 0 || nu <= 0 || N <= 0) return 2;
     long n = oracle_kkt_dim(nx, nu, N);
     long nz = (long)N * nx + (long)(N - 1) * nu;
@@ -156,7 +166,7 @@ int oracle_kkt_solve(int nx, int nu, int N, const double *A, const double *B,
     m.ab = (double *)calloc((size_t)n * m.w, sizeof(double));
     double *b = (double *)malloc((size_t)n * sizeof(double));
     if (!m.ab || !b) { free(m.ab); free(b); return 3; }
-    assemble(&m, nx, nu, N, A, B, Qd, Rd);
+    assemble(&m, nx, nu, N, A, B, Qd, Rd, Q, R);
     /* natural -> interleaved */
     for (int k = 0; k < N; ++k) {
         long bl = knot_base(k, nx, nu);
@@ -182,4 +192,10 @@ int oracle_kkt_solve(int nx, int nu, int N, const double *A, const double *B,
     free(m.ab);
     free(b);
     return st;
+}
+
+/* The diagonal-cost form. */
+int oracle_kkt_solve(int nx, int nu, int N, const double *A, const double *B,
+                     const double *Qd, const double *Rd, const double *h, double *y) {
+    return oracle_kkt_solve_g(nx, nu, N, A, B, Qd, Rd, NULL, NULL, h, y);
 }

@@ -56,6 +56,9 @@ def _load():
         lib.oracle_kkt_solve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          dp, dp, dp, dp, dp, dp]
         lib.oracle_kkt_solve.restype = ctypes.c_int
+        lib.oracle_kkt_solve_g.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           dp, dp, dp, dp, dp, dp, dp, dp]
+        lib.oracle_kkt_solve_g.restype = ctypes.c_int
         lib.oracle_kkt_dim.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.oracle_kkt_dim.restype = ctypes.c_long
         _lib = lib
@@ -102,8 +105,13 @@ def kkt_solve_rhs(lq, h: np.ndarray) -> np.ndarray:
     A, B, Qd, Rd = (_f64(getattr(lq, f)) for f in ("A", "B", "Qd", "Rd"))
     h = _f64(h).copy()
     y = np.empty_like(h)
-    st = lib.oracle_kkt_solve(lq.nx, lq.nu, lq.N, _dp(A), _dp(B), _dp(Qd), _dp(Rd),
-                              _dp(h), _dp(y))
+    if _dense(lq):
+        Q, R = _f64(lq.Q), _f64(lq.R)
+        st = lib.oracle_kkt_solve_g(lq.nx, lq.nu, lq.N, _dp(A), _dp(B), _dp(Qd), _dp(Rd),
+                                    _dp(Q), _dp(R), _dp(h), _dp(y))
+    else:
+        st = lib.oracle_kkt_solve(lq.nx, lq.nu, lq.N, _dp(A), _dp(B), _dp(Qd), _dp(Rd),
+                                  _dp(h), _dp(y))
     if st != 0:
         raise RuntimeError(f"oracle KKT solve failed with status {st}")
     return y
@@ -152,8 +160,32 @@ def _C_sparse(lq) -> sp.csr_matrix:
     return sp.csr_matrix((vals, (rows, cols)), shape=(N * nx, nz))
 
 
+def _dense(lq) -> bool:
+    return getattr(lq, "Q", None) is not None
+
+
 def _G_diag(lq) -> np.ndarray:
     return natural_z(_f64(lq.Qd), _f64(lq.Rd))
+
+
+def _Ginv_sparse(lq) -> sp.csr_matrix:
+    """G^-1 = blockdiag(Q_0^-1, R_0^-1, ..., Q_{N-1}^-1): reciprocals of the
+    diagonals, or inverses of the dense SPD cost blocks."""
+    if not _dense(lq):
+        return sp.diags(1.0 / _G_diag(lq)).tocsr()
+    Q, R = _f64(lq.Q), _f64(lq.R)
+    rows, cols, vals = [], [], []
+    o = 0
+    for k in range(lq.N):
+        for M in ([Q[k], R[k]] if k < lq.N - 1 else [Q[k]]):
+            n = M.shape[0]
+            ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+            rows.append((o + ii).ravel())
+            cols.append((o + jj).ravel())
+            vals.append(np.linalg.inv(M).ravel())
+            o += n
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(o, o))
 
 
 def _g_vec(lq) -> np.ndarray:
@@ -168,9 +200,9 @@ def schur_blocks(lq):
     """
     nx, N = lq.nx, lq.N
     C = _C_sparse(lq)
-    Ginv = sp.diags(1.0 / _G_diag(lq))
+    Ginv = _Ginv_sparse(lq)
     S = (C @ Ginv @ C.T).toarray() if N * nx <= 4096 else (C @ Ginv @ C.T).tocsr()
-    gamma = _f64(lq.c).ravel() - C @ (_g_vec(lq) / _G_diag(lq))
+    gamma = _f64(lq.c).ravel() - C @ (Ginv @ _g_vec(lq))
     Sd = np.empty((N, nx, nx))
     So = np.empty((max(N - 1, 0), nx, nx))
     for k in range(N):
@@ -219,7 +251,7 @@ def block_tridiag_sparse(Dd: np.ndarray, Do: np.ndarray) -> sp.csr_matrix:
 def dense_S(lq) -> np.ndarray:
     """Dense S+ = C G^-1 C^T (small problems only)."""
     C = _C_sparse(lq).toarray()
-    return C @ np.diag(1.0 / _G_diag(lq)) @ C.T
+    return C @ _Ginv_sparse(lq).toarray() @ C.T
 
 
 def dense_Phi_inv(Sd: np.ndarray, So: np.ndarray) -> np.ndarray:
@@ -282,7 +314,7 @@ def pcg(Sd, So, Pd, Po, b, lam0=None, tol=1e-6, tol_mode=0, max_iter=None):
 def recover(lq, lam: np.ndarray):
     """dz = -G^-1 (g - C^T lambda) (Eq. schur), by definition."""
     C = _C_sparse(lq)
-    z = -(_g_vec(lq) - C.T @ _f64(lam).ravel()) / _G_diag(lq)
+    z = -(_Ginv_sparse(lq) @ (_g_vec(lq) - C.T @ _f64(lam).ravel()))
     return split_z(z, lq.nx, lq.nu, lq.N)
 
 
@@ -304,6 +336,8 @@ def grad(lq, lam, dx, du, l_lam, l_dx, l_du):
                     transposed position)     ->  a_lam,k+1 y_z^T + lam_{k+1} a_z^T
     Returns a dict with the layouts of the inputs.
     """
+    if _dense(lq):
+        raise NotImplementedError("the gradient is stated for diagonal cost blocks")
     nx, nu, N = lq.nx, lq.nu, lq.N
     nz = N * nx + (N - 1) * nu
     yz = -natural_z(_f64(dx), _f64(du))

@@ -21,13 +21,22 @@ def dense_kkt(lq):
     def ui(k):
         return k * (nx + nu) + nx
 
+    dense = getattr(lq, "Q", None) is not None
     for k in range(N):
         for i in range(nx):
-            K[xi(k) + i, xi(k) + i] = lq.Qd[k][i]
+            if dense:
+                for j in range(nx):
+                    K[xi(k) + i, xi(k) + j] = lq.Q[k][i][j]
+            else:
+                K[xi(k) + i, xi(k) + i] = lq.Qd[k][i]
             h[xi(k) + i] = lq.q[k][i]
         if k < N - 1:
             for i in range(nu):
-                K[ui(k) + i, ui(k) + i] = lq.Rd[k][i]
+                if dense:
+                    for j in range(nu):
+                        K[ui(k) + i, ui(k) + j] = lq.R[k][i][j]
+                else:
+                    K[ui(k) + i, ui(k) + i] = lq.Rd[k][i]
                 h[ui(k) + i] = lq.r[k][i]
     C = np.zeros((N * nx, nz))
     C[0:nx, xi(0):xi(0) + nx] = np.eye(nx)
@@ -53,8 +62,12 @@ def riccati(lq):
     nx, nu, N = lq.nx, lq.nu, lq.N
     A = np.asarray(lq.A, np.float64)
     B = np.asarray(lq.B, np.float64)
-    Q = [np.diag(np.asarray(lq.Qd[k], np.float64)) for k in range(N)]
-    R = [np.diag(np.asarray(lq.Rd[k], np.float64)) for k in range(N - 1)]
+    if getattr(lq, "Q", None) is not None:
+        Q = [np.asarray(lq.Q[k], np.float64) for k in range(N)]
+        R = [np.asarray(lq.R[k], np.float64) for k in range(N - 1)]
+    else:
+        Q = [np.diag(np.asarray(lq.Qd[k], np.float64)) for k in range(N)]
+        R = [np.diag(np.asarray(lq.Rd[k], np.float64)) for k in range(N - 1)]
     q = np.asarray(lq.q, np.float64)
     r = np.asarray(lq.r, np.float64)
     c = np.asarray(lq.c, np.float64)

@@ -56,10 +56,11 @@ def test_golden_scalar_two_knot_blocks():
 
 
 # ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("dense", [False, True])
 @pytest.mark.parametrize("nx,nu,N,seed", [(2, 1, 1, 0), (2, 1, 2, 1), (4, 2, 5, 2),
                                           (14, 7, 8, 3), (36, 12, 3, 4), (6, 3, 8, 5)])
-def test_kkt_vs_dense_solve(nx, nu, N, seed):
-    lq = gen.kuka_lq(nx, nu, N, seed)
+def test_kkt_vs_dense_solve(nx, nu, N, seed, dense):
+    lq = gen.kuka_lq(nx, nu, N, seed, dense=dense)
     K, h, _ = dense_kkt(lq)
     y = np.linalg.solve(K, h)
     nz = N * nx + (N - 1) * nu
@@ -97,6 +98,8 @@ def test_kkt_exact_rational():
     (14, 7, 128, 130, {}),
     (14, 7, 512, 514, {}),
     (36, 12, 64, 5000, dict(dt=0.005, qd=(0.1, 100.0))),
+    (14, 7, 128, 131, dict(dense=True)),
+    (36, 12, 48, 5001, dict(dt=0.005, qd=(0.1, 100.0), dense=True)),
 ])
 def test_kkt_vs_riccati(nx, nu, N, seed, kw):
     lq = gen.kuka_lq(nx, nu, N, seed, **kw)
@@ -137,13 +140,21 @@ def test_schur_spd_and_precon_spd():
 
 
 # ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("dense", [False, True])
 @pytest.mark.parametrize("nx,nu,N,seed", [(14, 7, 9, 21), (4, 2, 6, 22), (36, 12, 4, 23)])
-def test_schur_closed_forms(nx, nu, N, seed):
-    """schur_blocks (sparse C G^-1 C^T) against Eq. trajoptSchur_1/2."""
-    lq = gen.kuka_lq(nx, nu, N, seed)
+def test_schur_closed_forms(nx, nu, N, seed, dense):
+    """schur_blocks (sparse C G^-1 C^T) against Eq. trajoptSchur_1/2; dense
+    cost blocks are inverted here through a Cholesky factorisation."""
+    import scipy.linalg as sla
+    lq = gen.kuka_lq(nx, nu, N, seed, dense=dense)
     Sd, So, gamma = oracle.schur_blocks(lq)
-    Qi = [np.diag(1.0 / lq.Qd[k]) for k in range(N)]
-    Ri = [np.diag(1.0 / lq.Rd[k]) for k in range(N - 1)]
+    if dense:
+        inv = lambda M: sla.cho_solve(sla.cho_factor(M), np.eye(M.shape[0]))
+        Qi = [inv(lq.Q[k]) for k in range(N)]
+        Ri = [inv(lq.R[k]) for k in range(N - 1)]
+    else:
+        Qi = [np.diag(1.0 / lq.Qd[k]) for k in range(N)]
+        Ri = [np.diag(1.0 / lq.Rd[k]) for k in range(N - 1)]
     np.testing.assert_allclose(Sd[0], Qi[0], atol=1e-14)
     np.testing.assert_allclose(gamma[0], lq.c[0] - Qi[0] @ lq.q[0], atol=1e-13)
     for k in range(N - 1):
@@ -323,3 +334,43 @@ def test_symmetric_stair_needs_fewer_iterations_than_block_jacobi():
     _, it_s, ok_s = oracle.pcg(Sd, So, *oracle.precon_blocks(Sd, So), -gamma, tol=1e-6)
     _, it_j, ok_j = oracle.pcg(Sd, So, *oracle.jacobi_blocks(Sd, So), -gamma, tol=1e-6)
     assert ok_s and ok_j and it_s < 0.7 * it_j, (it_s, it_j)
+
+
+
+# ---------------------------------------------------------------- dense SPD cost blocks
+def test_dense_blocks_with_diagonal_values_match_the_diagonal_problem():
+    """Q_k = diag(Qd_k), R_k = diag(Rd_k) given as dense blocks: the same
+    solution as the diagonal statement of the problem."""
+    lq = gen.kuka_lq(14, 7, 40, 41)
+    dq = lq.copy()
+    dq.Q = np.stack([np.diag(v) for v in lq.Qd])
+    dq.R = np.stack([np.diag(v) for v in lq.Rd])
+    a, b = oracle.kkt_solve(lq), oracle.kkt_solve(dq)
+    for x, y in zip(a, b):
+        assert oracle.relerr(y, x) < 1e-13
+
+
+def test_dense_invariants():
+    """Linearised dynamics and stationarity G dz + g - C^T lambda = 0 with
+    dense cost blocks."""
+    lq = gen.kuka_lq(14, 7, 64, 43, dense=True)
+    lam, dx, du = oracle.kkt_solve(lq)
+    res = dx[1:] - np.einsum("kij,kj->ki", lq.A, dx[:-1]) - np.einsum("kij,kj->ki", lq.B, du) + lq.c[1:]
+    assert np.abs(res).max() < 1e-11 and np.abs(dx[0] + lq.c[0]).max() < 1e-12
+    sx = np.einsum("kij,kj->ki", lq.Q, dx) + lq.q - lam
+    sx[:-1] += np.einsum("kji,kj->ki", lq.A, lam[1:])
+    su = np.einsum("kij,kj->ki", lq.R, du) + lq.r + np.einsum("kji,kj->ki", lq.B, lam[1:])
+    sc = max(1.0, np.abs(lam).max() * 10)
+    assert np.abs(sx).max() < 1e-11 * sc and np.abs(su).max() < 1e-11 * sc
+
+
+def test_dense_schur_route_reaches_kkt_solution():
+    lq = gen.kuka_lq(14, 7, 48, 47, dense=True)
+    Sd, So, gamma = oracle.schur_blocks(lq)
+    S = oracle.block_tridiag_sparse(Sd, So).toarray()
+    np.linalg.cholesky(S)
+    lam_s = np.linalg.solve(S, -gamma.ravel()).reshape(lq.N, lq.nx)
+    lam, dx, du = oracle.kkt_solve(lq)
+    assert oracle.relerr(lam_s, lam) < 1e-11
+    dx2, du2 = oracle.recover(lq, lam)
+    assert oracle.relerr(dx2, dx) < 1e-12 and oracle.relerr(du2, du) < 1e-12

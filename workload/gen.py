@@ -18,6 +18,7 @@ u_0..u_{N-2}.  Array layouts (row-major, float64 master copies):
 
     A[N-1][nx][nx]  B[N-1][nx][nu]  Qd[N][nx]  Rd[N-1][nu]
     q[N][nx]        r[N-1][nu]      c[N][nx]
+    Q[N][nx][nx]    R[N-1][nu][nu]  (optional dense SPD cost blocks)
 
 Draw order per instance (numpy default_rng(seed)): M, Dm, L, Qd, Rd, q, r, c.
 No solver arithmetic lives here.
@@ -25,7 +26,7 @@ No solver arithmetic lives here.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import List, Sequence
+from typing import List, Optional, Sequence
 
 import numpy as np
 
@@ -58,19 +59,35 @@ class LQ:
     q: np.ndarray
     r: np.ndarray
     c: np.ndarray
+    # optional dense SPD cost blocks Q[N][nx][nx], R[N-1][nu][nu] (the
+    # general Q_k, R_k of Sec. II-A); when present, Qd and Rd hold their
+    # diagonals and the dense blocks define the problem
+    Q: Optional[np.ndarray] = None
+    R: Optional[np.ndarray] = None
 
     FIELDS = ("A", "B", "Qd", "Rd", "q", "r", "c")
+    DENSE = ("Q", "R")
 
     @property
     def dtype(self):
         return self.A.dtype
 
+    @property
+    def dense(self) -> bool:
+        return self.Q is not None
+
     def astype(self, dt) -> "LQ":
         kw = {f: np.ascontiguousarray(getattr(self, f), dtype=dt) for f in self.FIELDS}
+        for f in self.DENSE:
+            v = getattr(self, f)
+            kw[f] = None if v is None else np.ascontiguousarray(v, dtype=dt)
         return LQ(self.nx, self.nu, self.N, **kw)
 
     def copy(self) -> "LQ":
         kw = {f: np.array(getattr(self, f), copy=True) for f in self.FIELDS}
+        for f in self.DENSE:
+            v = getattr(self, f)
+            kw[f] = None if v is None else np.array(v, copy=True)
         return LQ(self.nx, self.nu, self.N, **kw)
 
 
@@ -80,8 +97,10 @@ def to_f32(lq: LQ) -> LQ:
 
 
 def kuka_lq(nx: int, nu: int, N: int, seed: int, dt: float = 0.01,
-            qd=(1.0, 10.0), rd=(0.01, 0.1)) -> LQ:
-    """Draw one Kuka-shaped LQ subproblem (float64)."""
+            qd=(1.0, 10.0), rd=(0.01, 0.1), dense: bool = False) -> LQ:
+    """Draw one Kuka-shaped LQ subproblem (float64).  dense=True adds general
+    SPD cost blocks Q_k = diag(Qd_k) + (0.5/nx) W W^T and R_k = diag(Rd_k) +
+    (0.01/nu) V V^T with W, V ~ N(0, 1)."""
     if nx % 2 or not (1 <= nu <= nx // 2) or N < 1:
         raise ValueError("need even nx, 1 <= nu <= nx/2 and N >= 1")
     h = nx // 2
@@ -104,7 +123,21 @@ def kuka_lq(nx: int, nu: int, N: int, seed: int, dt: float = 0.01,
     Minv = np.einsum("kij,klj->kil", L, L) + 0.1 * eye
     B = np.zeros((K, nx, nu))
     B[:, h:, :] = dt * Minv[:, :, :nu]
-    return LQ(nx, nu, N, A, B, Qd, Rd, q, r, c)
+    lq = LQ(nx, nu, N, A, B, Qd, Rd, q, r, c)
+    if dense:
+        # general SPD cost blocks: the drawn diagonals plus a random
+        # positive semidefinite coupling (drawn after everything above, so
+        # A, B, q, r, c match the diagonal instance of the same seed)
+        Wq = rng.normal(0.0, 1.0, size=(N, nx, nx))
+        Wr = rng.normal(0.0, 1.0, size=(K, nu, nu))
+        Q = np.einsum("kij,klj->kil", Wq, Wq) * (0.5 / nx)
+        R = np.einsum("kij,klj->kil", Wr, Wr) * (0.01 / nu)
+        Q[:, np.arange(nx), np.arange(nx)] += Qd
+        R[:, np.arange(nu), np.arange(nu)] += Rd
+        lq.Q, lq.R = Q, R
+        lq.Qd = np.ascontiguousarray(Q[:, np.arange(nx), np.arange(nx)])
+        lq.Rd = np.ascontiguousarray(R[:, np.arange(nu), np.arange(nu)])
+    return lq
 
 
 @dataclass
@@ -141,6 +174,11 @@ def concat_batch(items: Sequence[LQ]) -> LQBatch:
     knot_off[1:] = np.cumsum(Ns)
     cat = {f: np.ascontiguousarray(np.concatenate([getattr(it, f) for it in items], axis=0))
            for f in LQ.FIELDS}
+    if all(it.dense for it in items):
+        for f in LQ.DENSE:
+            cat[f] = np.ascontiguousarray(np.concatenate([getattr(it, f) for it in items], axis=0))
+    elif any(it.dense for it in items):
+        raise ValueError("a batch mixes dense and diagonal cost blocks")
     lq = LQ(nx, nu, int(knot_off[-1]), **cat)
     return LQBatch(nx, nu, Ns, knot_off, lq, list(items))
 
@@ -151,8 +189,9 @@ def batch_horizons(B: int, lo: int, hi: int, seed: int) -> np.ndarray:
 
 
 def kuka_batch(nx: int, nu: int, Ns: Sequence[int], seed_base: int, dt: float = 0.01,
-               qd=(1.0, 10.0)) -> LQBatch:
-    items = [kuka_lq(nx, nu, int(n), seed_base + i, dt=dt, qd=qd) for i, n in enumerate(Ns)]
+               qd=(1.0, 10.0), dense: bool = False) -> LQBatch:
+    items = [kuka_lq(nx, nu, int(n), seed_base + i, dt=dt, qd=qd, dense=dense)
+             for i, n in enumerate(Ns)]
     return concat_batch(items)
 
 
