@@ -81,6 +81,14 @@ typedef struct {
 
 typedef struct {
     const void *A, *B, *Qd, *Rd, *q, *r, *c;
+    /* Optional general cost blocks (the Q_k, R_k of Sec. II-A's QP as full
+       matrices): Q[N][nx][nx], R[N-1][nu][nu], symmetric positive definite,
+       row-major.  When Q is not NULL, form_schur and recover_step use Q and
+       R (R required when N > 1) and ignore Qd and Rd (which may be NULL); a
+       block that is not SPD marks its instance MPCG_INFO_BADINPUT.
+       refine_step and backward support diagonal costs only and return
+       MPCG_EUNSUPPORTED for dense blocks.  NULL: diagonal Qd, Rd. */
+    const void *Q, *R;
 } mpcg_lq;
 
 typedef struct {

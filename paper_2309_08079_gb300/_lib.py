@@ -41,7 +41,7 @@ class mpcg_dims(C.Structure):
 
 
 class mpcg_lq(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("A", "B", "Qd", "Rd", "q", "r", "c")]
+    _fields_ = [(n, C.c_void_p) for n in ("A", "B", "Qd", "Rd", "q", "r", "c", "Q", "R")]
 
 
 class mpcg_schur(C.Structure):

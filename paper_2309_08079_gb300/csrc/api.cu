@@ -190,6 +190,8 @@ int form_schur_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off,
     a.A = (const T *)lq->A; a.B = (const T *)lq->B; a.Qd = (const T *)lq->Qd;
     a.Rd = (const T *)lq->Rd; a.q = (const T *)lq->q; a.r = (const T *)lq->r;
     a.c = (const T *)lq->c;
+    a.Qf = (const T *)lq->Q;
+    a.Rf = (const T *)lq->R;
     a.Sd = (T *)s->Sd; a.So = (T *)s->So; a.gamma = (T *)s->gamma;
     a.info = s->info;
     if (s->info) {
@@ -296,6 +298,13 @@ int solve_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off,
 template <typename T>
 int recover_t(const mpcg_dims &d, int B, const int *knot_off, const mpcg_lq *lq,
                      const void *lam, void *dx, void *du, cudaStream_t st) {
+    if (lq->Q)
+        return err_cuda(launch_recover_dense<T>(d.nx, d.nu, make_bv(knot_off, B, d.N),
+                                                knot_off ? B * d.N : d.N, (const T *)lq->A,
+                                                (const T *)lq->B, (const T *)lq->Q,
+                                                (const T *)lq->R, (const T *)lq->q,
+                                                (const T *)lq->r, (const T *)lam, (T *)dx,
+                                                (T *)du, st));
     return err_cuda(launch_recover<T>(d.nx, d.nu, make_bv(knot_off, B, d.N),
                                       knot_off ? B * d.N : d.N, (const T *)lq->A,
                                       (const T *)lq->B, (const T *)lq->Qd, (const T *)lq->Rd,
@@ -327,7 +336,9 @@ int refine_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, con
 // Per-control arrays (A, B, Rd, r) are empty, and may be NULL, when every
 // horizon is 1 (dims.N == 1).
 bool lq_ok(const mpcg_lq *lq, const mpcg_dims &d) {
-    if (!lq || !lq->Qd || !lq->q || !lq->c) return false;
+    if (!lq || !lq->q || !lq->c) return false;
+    if (lq->Q) return d.N == 1 || (lq->A && lq->B && lq->R && lq->r);
+    if (!lq->Qd) return false;
     return d.N == 1 || (lq->A && lq->B && lq->Rd && lq->r);
 }
 
@@ -347,7 +358,7 @@ const char *mpcg_strerror(int code) {
         case MPCG_NOT_CONVERGED: return "not converged within max_iter";
         case MPCG_BREAKDOWN: return "breakdown: p^T S p <= 0 or not finite";
         case MPCG_NONFINITE: return "residual not finite";
-        case MPCG_BADINPUT: return "bad input: Qd or Rd not positive and finite";
+        case MPCG_BADINPUT: return "bad input: a cost block not positive definite (or Qd, Rd not positive and finite)";
         case MPCG_TIMEOUT: return "bounded device wait gave up";
         default: return "unknown code";
     }
@@ -446,6 +457,7 @@ int mpcg_refine_step_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot
     if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !s->Sd ||
         !s->Pd || (d.N > 1 && (!s->So || !s->Po)) || !lambda || !workspace)
         return MPCG_EINVAL;
+    if (lq->Q) return MPCG_EUNSUPPORTED;  // the exact residual is stated for diagonal costs
     if (d.dtype == 1)
         return refine_t<double>(h, d, B, knot_off, lq, s, (double *)lambda, opts, stats, workspace,
                                 (cudaStream_t)stream);
@@ -468,6 +480,7 @@ int mpcg_backward_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_of
         !lam_bar || !dx_bar || !g || !g->A || !g->B || !g->Qd || !g->Rd || !g->q || !g->r ||
         !g->c || !workspace || (d.N > 1 && (!du || !du_bar)))
         return MPCG_EINVAL;
+    if (lq->Q) return MPCG_EUNSUPPORTED;  // gradients are stated for diagonal costs
     if (d.dtype == 1)
         return backward_t<double>(h, d, B, knot_off, lq, s, (const double *)lambda,
                                   (const double *)dx, (const double *)du, (const double *)lam_bar,
@@ -536,6 +549,7 @@ extern "C" int mpcg_backward_batched_noalloc(mpcg_handle *h, mpcg_dims d, int B,
         !lam_bar || !dx_bar || !g || !g->A || !g->B || !g->Qd || !g->Rd || !g->q || !g->r ||
         !g->c || (d.N > 1 && (!du || !du_bar)))
         return MPCG_EINVAL;
+    if (lq->Q) return MPCG_EUNSUPPORTED;  // gradients are stated for diagonal costs
     const size_t need = mpcg_workspace_bytes(d, B);
     if (need == 0) return MPCG_EINVAL;
     if (need > MPCG_NOALLOC_SCRATCH_BYTES) {

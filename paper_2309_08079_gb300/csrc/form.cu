@@ -422,6 +422,202 @@ __global__ void axpy_kernel(int nx, BatchView bv, const T *__restrict__ d, T *__
 }
 
 // ---------------------------------------------------------------------------
+// General SPD cost blocks (the Q_k, R_k of Sec. II-A's QP as full matrices).
+// A group inverts its blocks in shared memory by Gauss-Jordan elimination
+// without pivoting (positive pivots are exactly the SPD condition), then
+// forms Eq. trajoptSchur_1/2 with the inverses:
+//   theta_k = A_k Q_k^-1 A_k^T + B_k R_k^-1 B_k^T + Q_{k+1}^-1,
+//   phi_k = -A_k Q_k^-1,
+//   zeta_k = -A_k Q_k^-1 q_k - B_k R_k^-1 r_k + Q_{k+1}^-1 q_{k+1}.
+// ---------------------------------------------------------------------------
+
+// In-place inverse of the n x n SPD block M (group of G threads; all of them
+// call it).  Returns true (in every thread) when a pivot is not positive and
+// finite, i.e. M is not SPD.  The result is symmetrised.
+template <typename T>
+__device__ bool gj_inverse_spd(T *M, int n, int G, int t) {
+    bool bad = false;
+    for (int j = 0; j < n; ++j) {
+        const T piv = M[j * n + j];
+        bad |= !(piv > T(0) && isfinite((double)piv));
+        const T d = T(1) / piv;
+        for (int c = t; c < n; c += G)
+            if (c != j) M[j * n + c] *= d;
+        group_sync(G);
+        const int n1 = n - 1;
+        for (int e = t; e < n1 * n1; e += G) {
+            int i = e / n1, c = e % n1;
+            i += (i >= j);
+            c += (c >= j);
+            M[i * n + c] -= M[i * n + j] * M[j * n + c];
+        }
+        group_sync(G);
+        for (int i = t; i < n; i += G) {
+            if (i != j) M[i * n + j] = -M[i * n + j] * d;
+            else M[j * n + j] = d;
+        }
+        group_sync(G);
+    }
+    for (int e = t; e < n * n; e += G) {
+        const int i = e / n, c = e % n;
+        if (i < c) {
+            const T v = T(0.5) * (M[i * n + c] + M[c * n + i]);
+            M[i * n + c] = v;
+            M[c * n + i] = v;
+        }
+    }
+    group_sync(G);
+    return bad;
+}
+
+template <typename T>
+__host__ __device__ inline size_t dense_form_words(int nx, int nu) {
+    return (size_t)4 * nx * nx + (size_t)nu * nu + (size_t)2 * nx * nu + 2 * nx + nu;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FORM_THREADS) form_schur_dense_kernel(const SchurArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = a.nx, nu = a.nu;
+    const int G = group_size(nx);
+    const int groups = FORM_THREADS / G;
+    const int g = threadIdx.x / G, t = threadIdx.x % G;
+    const int kg = blockIdx.x * groups + g;
+    const int n2 = nx * nx;
+    T *Qi0 = reinterpret_cast<T *>(smem_raw) + dense_form_words<T>(nx, nu) * g;
+    T *Qi1 = Qi0 + n2, *Am = Qi1 + n2, *As = Am + n2, *Ri = As + n2, *Bm = Ri + nu * nu,
+      *Bs = Bm + nx * nu, *q0 = Bs + nx * nu, *q1 = q0 + nx, *rr = q1 + nx;
+    if (kg >= a.bv.total()) return;  // whole group leaves together
+    const int b = a.bv.owner(kg);
+    int k0, Nb;
+    a.bv.range(b, k0, Nb);
+    const int k = kg - k0;
+    const int j = kg - b - 1;  // control index of (A, B, R, r, So) for this row (k > 0)
+    for (int e = t; e < n2; e += G) Qi1[e] = a.Qf[(size_t)kg * n2 + e];
+    for (int i = t; i < nx; i += G) q1[i] = a.q[(size_t)kg * nx + i];
+    if (k > 0) {
+        for (int e = t; e < n2; e += G) {
+            Qi0[e] = a.Qf[(size_t)(kg - 1) * n2 + e];
+            Am[e] = a.A[(size_t)j * n2 + e];
+        }
+        for (int e = t; e < nu * nu; e += G) Ri[e] = a.Rf[(size_t)j * nu * nu + e];
+        for (int e = t; e < nx * nu; e += G) Bm[e] = a.B[(size_t)j * nx * nu + e];
+        for (int i = t; i < nx; i += G) q0[i] = a.q[(size_t)(kg - 1) * nx + i];
+        for (int i = t; i < nu; i += G) rr[i] = a.r[(size_t)j * nu + i];
+    }
+    group_sync(G);
+    bool bad = gj_inverse_spd(Qi1, nx, G, t);
+    if (k == 0) {
+        T *Sd = a.Sd + (size_t)kg * n2;
+        for (int e = t; e < n2; e += G) Sd[e] = Qi1[e];
+        for (int i = t; i < nx; i += G) {
+            T z = T(0);
+            for (int m = 0; m < nx; ++m) z += Qi1[i * nx + m] * q1[m];
+            a.gamma[(size_t)kg * nx + i] = a.c[(size_t)kg * nx + i] - z;
+        }
+    } else {
+        bad |= gj_inverse_spd(Qi0, nx, G, t);
+        bad |= gj_inverse_spd(Ri, nu, G, t);
+        for (int e = t; e < n2; e += G) {  // As = A Q_{k-1}^-1
+            const int i = e / nx, c = e % nx;
+            T s = T(0);
+            for (int m = 0; m < nx; ++m) s += Am[i * nx + m] * Qi0[m * nx + c];
+            As[e] = s;
+        }
+        for (int e = t; e < nx * nu; e += G) {  // Bs = B R^-1
+            const int i = e / nu, c = e % nu;
+            T s = T(0);
+            for (int m = 0; m < nu; ++m) s += Bm[i * nu + m] * Ri[m * nu + c];
+            Bs[e] = s;
+        }
+        group_sync(G);
+        T *Sd = a.Sd + (size_t)kg * n2;
+        T *So = a.So + (size_t)j * n2;
+        // theta (upper triangle computed once, mirrored: exactly symmetric)
+        for (int e = t; e < n2; e += G) {
+            const int i = e / nx, jj = e % nx;
+            So[e] = -As[e];
+            if (i > jj) continue;
+            T s = Qi1[i * nx + jj];
+            for (int m = 0; m < nx; ++m) s += As[i * nx + m] * Am[jj * nx + m];
+            for (int m = 0; m < nu; ++m) s += Bs[i * nu + m] * Bm[jj * nu + m];
+            Sd[i * nx + jj] = s;
+            Sd[jj * nx + i] = s;
+        }
+        for (int i = t; i < nx; i += G) {
+            T z = T(0);
+            for (int m = 0; m < nx; ++m) z += Qi1[i * nx + m] * q1[m] - As[i * nx + m] * q0[m];
+            for (int m = 0; m < nu; ++m) z -= Bs[i * nu + m] * rr[m];
+            a.gamma[(size_t)kg * nx + i] = a.c[(size_t)kg * nx + i] - z;
+        }
+    }
+    if (a.info && bad && t == 0) atomicOr(&a.info[b], MPCG_INFO_BADINPUT);
+}
+
+// recover with dense cost blocks: zx_k = Q_k^-1 (v_k - A_k^T v_{k+1} - hx_k),
+// zu_k = R_k^-1 (-B_k^T v_{k+1} - hu_k); the right-hand sides are summed with
+// exact products in extended precision (they cancel when v is large against
+// z), the products with the inverses likewise, each rounded once.
+template <typename T>
+__global__ void __launch_bounds__(FORM_THREADS)
+recover_dense_kernel(int nx, int nu, BatchView bv, const T *__restrict__ A,
+                     const T *__restrict__ B, const T *__restrict__ Qf, const T *__restrict__ Rf,
+                     const T *__restrict__ hx, const T *__restrict__ hu, const T *__restrict__ v,
+                     T *__restrict__ zx, T *__restrict__ zu) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int G = group_size(nx);
+    const int groups = FORM_THREADS / G;
+    const int g = threadIdx.x / G, t = threadIdx.x % G;
+    const int kg = blockIdx.x * groups + g;
+    const int n2 = nx * nx;
+    T *Qi = reinterpret_cast<T *>(smem_raw) + ((size_t)n2 + nu * nu + 2 * nx + nu) * g;
+    T *Ri = Qi + n2, *vn = Ri + nu * nu, *sx = vn + nx, *su = sx + nx;
+    if (kg >= bv.total()) return;
+    const int b = bv.owner(kg);
+    int k0, Nb;
+    bv.range(b, k0, Nb);
+    const bool last = kg - k0 + 1 >= Nb;
+    const int j = kg - b;
+    for (int e = t; e < n2; e += G) Qi[e] = Qf[(size_t)kg * n2 + e];
+    if (!last)
+        for (int e = t; e < nu * nu; e += G) Ri[e] = Rf[(size_t)j * nu * nu + e];
+    for (int i = t; i < nx; i += G) vn[i] = last ? T(0) : v[(size_t)(kg + 1) * nx + i];
+    group_sync(G);
+    gj_inverse_spd(Qi, nx, G, t);
+    if (!last) gj_inverse_spd(Ri, nu, G, t);
+    using AT = Acc<T>;
+    for (int i = t; i < nx + nu; i += G) {
+        if (i < nx) {
+            auto s = AT::add(AT::from(v[(size_t)kg * nx + i]), AT::from(-hx[(size_t)kg * nx + i]));
+            if (!last) {
+                const T *Ak = A + (size_t)j * n2;
+                for (int m = 0; m < nx; ++m) s = AT::add(s, AT::prod(-Ak[m * nx + i], vn[m]));
+            }
+            sx[i] = AT::to_T(s);
+        } else if (!last) {
+            const int u = i - nx;
+            const T *Bk = B + (size_t)j * nx * nu;
+            auto s = AT::from(-hu[(size_t)j * nu + u]);
+            for (int m = 0; m < nx; ++m) s = AT::add(s, AT::prod(-Bk[m * nu + u], vn[m]));
+            su[u] = AT::to_T(s);
+        }
+    }
+    group_sync(G);
+    for (int i = t; i < nx + nu; i += G) {
+        if (i < nx) {
+            auto s = AT::zero();
+            for (int m = 0; m < nx; ++m) s = AT::add(s, AT::prod(Qi[i * nx + m], sx[m]));
+            zx[(size_t)kg * nx + i] = AT::to_T(s);
+        } else if (!last) {
+            const int u = i - nx;
+            auto s = AT::zero();
+            for (int m = 0; m < nu; ++m) s = AT::add(s, AT::prod(Ri[u * nu + m], su[m]));
+            zu[(size_t)j * nu + u] = AT::to_T(s);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
 static inline int form_grid(int nx, int Ktot) {
@@ -432,6 +628,11 @@ static inline int form_grid(int nx, int Ktot) {
 template <typename T>
 cudaError_t launch_form_schur(const SchurArgs<T> &a, cudaStream_t s) {
     const int G = group_size(a.nx);
+    if (a.Qf) {
+        const size_t smem = dense_form_words<T>(a.nx, a.nu) * sizeof(T) * (FORM_THREADS / G);
+        form_schur_dense_kernel<T><<<form_grid(a.nx, a.Kgrid), FORM_THREADS, smem, s>>>(a);
+        return cudaGetLastError();
+    }
     const size_t per = (size_t)2 * a.nx * a.nx + 2 * a.nx * a.nu + 4 * a.nx + 2 * a.nu;
     const size_t smem = per * sizeof(T) * (FORM_THREADS / G);
     form_schur_kernel<T><<<form_grid(a.nx, a.Kgrid), FORM_THREADS, smem, s>>>(a);
@@ -458,6 +659,17 @@ cudaError_t launch_recover(int nx, int nu, BatchView bv, int Kgrid, const T *A, 
     const int groups = FORM_THREADS / group_size(nx);
     recover_kernel<T><<<form_grid(nx, Kgrid), FORM_THREADS, sizeof(T) * nx * groups, s>>>(
         nx, nu, bv, A, B, Qd, Rd, hx, hu, v, zx, zu);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_recover_dense(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B,
+                                 const T *Qf, const T *Rf, const T *hx, const T *hu, const T *v,
+                                 T *zx, T *zu, cudaStream_t s) {
+    const int groups = FORM_THREADS / group_size(nx);
+    const size_t smem = sizeof(T) * ((size_t)nx * nx + nu * nu + 2 * nx + nu) * groups;
+    recover_dense_kernel<T><<<form_grid(nx, Kgrid), FORM_THREADS, smem, s>>>(
+        nx, nu, bv, A, B, Qf, Rf, hx, hu, v, zx, zu);
     return cudaGetLastError();
 }
 
@@ -510,6 +722,8 @@ static cudaError_t form_prepare_t(int smem_optin) {
     if ((e = cudaFuncSetAttribute(precon_off_kernel<T>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(recover_kernel<T>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(resid_kernel<T>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(form_schur_dense_kernel<T>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(recover_dense_kernel<T>, a, smem_optin))) return e;
     return cudaFuncSetAttribute(cgh_kernel<T>, a, smem_optin);
 }
 
@@ -534,7 +748,10 @@ cudaError_t form_prepare(int smem_optin) {
     template cudaError_t launch_resid<T>(int, int, BatchView, int, const T *, const T *,          \
                                          const T *, const T *, const T *, const T *, const T *,   \
                                          const T *, T *, cudaStream_t);                           \
-    template cudaError_t launch_axpy<T>(int, BatchView, int, const T *, T *, cudaStream_t);
+    template cudaError_t launch_axpy<T>(int, BatchView, int, const T *, T *, cudaStream_t);     \
+    template cudaError_t launch_recover_dense<T>(int, int, BatchView, int, const T *, const T *, \
+                                                 const T *, const T *, const T *, const T *,     \
+                                                 const T *, T *, T *, cudaStream_t);
 MPCG_INST(float)
 MPCG_INST(double)
 #undef MPCG_INST

@@ -11,6 +11,7 @@ struct SchurArgs {
     BatchView bv;
     int Kgrid;  // host-side upper bound on the total knots (grid size only)
     const T *A, *B, *Qd, *Rd, *q, *r, *c;
+    const T *Qf, *Rf;  // dense SPD cost blocks (nullptr: diagonal Qd, Rd)
     T *Sd, *So, *gamma;
     unsigned *info;
 };
@@ -61,6 +62,10 @@ template <typename T>
 cudaError_t launch_recover(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B,
                            const T *Qd, const T *Rd, const T *hx, const T *hu, const T *v, T *zx,
                            T *zu, cudaStream_t s);
+template <typename T>
+cudaError_t launch_recover_dense(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B,
+                                 const T *Qf, const T *Rf, const T *hx, const T *hu, const T *v,
+                                 T *zx, T *zu, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cgh(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B,
                        const T *Qd, const T *Rd, const T *hx, const T *hu, const T *w, T *out,

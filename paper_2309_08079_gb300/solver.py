@@ -50,6 +50,8 @@ class LQTensors:
     nb: int = 1            # number of instances
     total: int = 0         # total knots
     Ns: Optional[np.ndarray] = None  # host copy of the horizons (batched)
+    Q: Optional[torch.Tensor] = None  # dense SPD cost blocks [N][nx][nx] (None: diagonal Qd)
+    R: Optional[torch.Tensor] = None  # dense SPD cost blocks [N-1][nu][nu]
 
     FIELDS = ("A", "B", "Qd", "Rd", "q", "r", "c")
 
@@ -69,14 +71,23 @@ class LQTensors:
         return L.mpcg_dims(self.nx, self.nu, self.N, _DT[self.dtype])
 
     def lq_struct(self) -> L.mpcg_lq:
+        dense = [None if t is None else t.data_ptr() for t in (self.Q, self.R)]
         return L.mpcg_lq(*(t.data_ptr() for t in (self.A, self.B, self.Qd, self.Rd, self.q,
-                                                   self.r, self.c)))
+                                                   self.r, self.c)), *dense)
+
+    @staticmethod
+    def _dense(src, device, dtype):
+        if getattr(src, "Q", None) is None:
+            return {}
+        return {f: torch.as_tensor(np.ascontiguousarray(getattr(src, f)), dtype=dtype, device=device)
+                for f in ("Q", "R")}
 
     @staticmethod
     def from_numpy(lq, device="cuda", dtype=torch.float32) -> "LQTensors":
         t = {f: torch.as_tensor(np.ascontiguousarray(getattr(lq, f)), dtype=dtype, device=device)
              for f in LQTensors.FIELDS}
-        return LQTensors(lq.nx, lq.nu, lq.N, **t, knot_off=None, nb=1, total=lq.N)
+        return LQTensors(lq.nx, lq.nu, lq.N, **t, knot_off=None, nb=1, total=lq.N,
+                         **LQTensors._dense(lq, device, dtype))
 
     @staticmethod
     def from_batch(batch, device="cuda", dtype=torch.float32) -> "LQTensors":
@@ -85,7 +96,8 @@ class LQTensors:
         ko = torch.as_tensor(batch.knot_off.astype(np.int32), device=device)
         return LQTensors(batch.nx, batch.nu, int(batch.Ns.max()), **t, knot_off=ko,
                          nb=batch.B, total=int(batch.knot_off[-1]),
-                         Ns=np.asarray(batch.Ns, dtype=np.int64).copy())
+                         Ns=np.asarray(batch.Ns, dtype=np.int64).copy(),
+                         **LQTensors._dense(batch.lq, device, dtype))
 
 
 @dataclass
