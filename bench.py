@@ -359,11 +359,12 @@ def run_ours(args, rank, world, local_rank):
                 "kernel": "pcg_cluster_kernel", "peak_source": peak_note,
                 "alg_bytes_per_launch": alg_bytes, "launch_us": pcg_s * 1e6}
 
-    batched = backward = sweep = exit_sweep = precon_compare = large = None
+    batched = backward = sweep = exit_sweep = precon_compare = dense_cost = large = None
     if not args.no_sweep:
         sweep = run_sweep(s, dev, args.sweep_reps, flush)
         exit_sweep = run_exit_sweep(s, dev, min(args.sweep_reps, 200))
         precon_compare = run_precon_compare(s, dev, min(args.sweep_reps, 100))
+        dense_cost = run_dense_cost(s, dev, min(args.sweep_reps, 50))
     if not args.no_batched:
         batched = run_batched(s, dev, args.batched_solves)
         backward = run_backward(s, dev)
@@ -404,7 +405,8 @@ def run_ours(args, rank, world, local_rank):
         "parity": {"err_lambda": err_lam, "err_dz": err_dz, "tol": 1e-4},
         "clocks": clk, "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roofline,
         "cpu_baseline": cpu, "batched": batched, "backward": backward, "sweep": sweep,
-        "exit_sweep": exit_sweep, "precon_compare": precon_compare, "large_state": large,
+        "exit_sweep": exit_sweep, "precon_compare": precon_compare, "dense_cost": dense_cost,
+        "large_state": large,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -794,6 +796,54 @@ def run_precon_compare(s, dev, reps):
                                    "err_lambda_vs_oracle": oracle.relerr(lams[reps - 1].cpu().double().numpy(), lo)}
     return {"workload": f"single instances N in (128, 512), nx={c['nx']}, {reps} warm-started PCG solves "
                         f"per preconditioner, rel. residual 1e-6", "per_case": out}
+
+
+def run_dense_cost(s, dev, reps):
+    """General SPD cost blocks Q_k, R_k (dense) against the diagonal costs of
+    the same instances, N = 128 and 512: µs per whole solve, the formation
+    share, iterations, error against the oracle."""
+    import torch
+    import oracle
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    c = gen.CONFIG_SWEEP
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for N in (128, 512):
+        for name, dense in (("diagonal", False), ("dense", True)):
+            lq = gen.kuka_lq(c["nx"], c["nu"], N, c["seed_base"] + N, dt=c["dt"], qd=c["qd"],
+                             dense=dense).astype(np.float32)
+            lo, xo, uo = oracle.kkt_solve(lq.astype(np.float64))
+            lt = LQTensors.from_numpy(lq, device=dev)
+            sch = s.alloc_schur(lt)
+            o = make_opts(tol=1e-6)
+            lam = torch.zeros(N, c["nx"], device=dev)
+            dx = torch.empty(N, c["nx"], device=dev)
+            du = torch.empty(max(N - 1, 1), c["nu"], device=dev)
+            st = s.alloc_stats(1, dev)
+            s.solve(lt, lam.clone(), opts=o, schur=sch)
+            torch.cuda.synchronize()
+            tim, frm = _step_timer(s, stream), _step_timer(s, stream)
+
+            def one():
+                lam.zero_()
+                frm(lambda: (s.form_schur(lt, sch), s.form_precon(lt, sch)))
+                s.pcg_solve(lt, sch, lam, o, st)
+                s.recover_step(lt, lam, dx, du)
+
+            for _ in range(reps):
+                tim(one)
+            torch.cuda.synchronize()
+            e_lam = oracle.relerr(lam.cpu().double().numpy(), lo)
+            e_dz = oracle.relerr(np.concatenate([dx.cpu().double().numpy().ravel(),
+                                                 du[:N - 1].cpu().double().numpy().ravel()]),
+                                 np.concatenate([xo.ravel(), uo.ravel()]))
+            out[f"N{N}_{name}"] = {"us_per_solve": pct(np.array(tim.ms()) * 1e3),
+                                   "form_precon_us": float(np.median(frm.ms())) * 1e3,
+                                   "iters": int(read_stats(st)["iters"][0]),
+                                   "converged": bool(read_stats(st)["status"][0] == 0),
+                                   "err_lambda": e_lam, "err_dz": e_dz}
+    return {"workload": f"single instances N in (128, 512), nx={c['nx']}, cold solves, "
+                        f"diagonal vs dense SPD cost blocks (same A, B, q, r, c)", "per_case": out}
 
 
 def run_large(s, dev, solves, B=None):
