@@ -10,3 +10,4 @@ from .oracle import (  # noqa: F401
     dense_S, dense_Phi_inv, block_tridiag_sparse, pcg, recover, grad, loss,
     solve_batch, natural_z, split_z, relerr,
 )
+from . import nmpc  # noqa: F401

@@ -213,3 +213,84 @@ def warm_start(lam_star: np.ndarray, seed: int, rep: int, rel: float = 0.01) -> 
 def loss_weights(n_lam: int, seed: int) -> np.ndarray:
     """w ~ N(0, 1) for the scalar loss sum ||dz||^2 + w^T lambda."""
     return np.random.default_rng(seed).normal(0.0, 1.0, size=n_lam)
+
+
+# ---------------------------------------------------------------------------
+# Synthetic nonlinear model for the SQP outer loop and the parallel line
+# search (Sec. II-A Step 3, Sec. IV-C).  The paper's experiments linearise
+# the Kuka rigid-body dynamics; that model is not available, so a
+# Kuka-shaped stand-in with the same state layout is used: h = nx/2 joints,
+# x = (joint positions p, joint velocities v), nu actuated joints,
+#     v+ = v + dt (P u - damp * v - stiff * sin(p)),   p+ = p + dt v+
+# (semi-implicit Euler), and a tracking cost
+#     l(x, u) = 1/2 sum wq (x - xref_k)^2 + 1/2 sum wr u^2,
+#     l_f(x)  = 1/2 sum wf (x - xref_{N-1})^2.
+# Only parameters and initial data are drawn here; the dynamics, their
+# Jacobians and the merit function live in the oracle and in the kernels.
+# ---------------------------------------------------------------------------
+@dataclass
+class Model:
+    nx: int
+    nu: int
+    dt: float
+    P: np.ndarray       # [h][nu] input matrix
+    damp: np.ndarray    # [h]
+    stiff: np.ndarray   # [h]
+    wq: np.ndarray      # [nx] stage state weights
+    wr: np.ndarray      # [nu] control weights
+    wf: np.ndarray      # [nx] terminal state weights
+
+    def astype(self, dt) -> "Model":
+        f = lambda a: np.ascontiguousarray(a, dtype=dt)
+        return Model(self.nx, self.nu, self.dt, f(self.P), f(self.damp), f(self.stiff),
+                     f(self.wq), f(self.wr), f(self.wf))
+
+
+@dataclass
+class Tracking:
+    """One tracking problem for the model: start state, reference, initial guess."""
+    N: int
+    xs: np.ndarray      # [nx]
+    xref: np.ndarray    # [N][nx]
+    X: np.ndarray       # [N][nx] initial state trajectory
+    U: np.ndarray       # [N-1][nu] initial controls
+
+    def astype(self, dt) -> "Tracking":
+        f = lambda a: np.ascontiguousarray(a, dtype=dt)
+        return Tracking(self.N, f(self.xs), f(self.xref), f(self.X), f(self.U))
+
+
+CONFIG_NMPC = dict(name="nmpc", nx=14, nu=7, Ns=(128, 512), model_seed=6, seed_base=6000,
+                   dt=0.01, n_alpha=9, sqp_iters=8)
+
+
+def nmpc_model(nx: int, nu: int, seed: int, dt: float = 0.01) -> Model:
+    if nx % 2 or not (1 <= nu <= nx // 2):
+        raise ValueError("need even nx and 1 <= nu <= nx/2")
+    h = nx // 2
+    rng = np.random.default_rng(seed)
+    L = rng.normal(0.0, 1.0, size=(h, h))
+    P = (L @ L.T + 0.1 * np.eye(h))[:, :nu]
+    damp = rng.uniform(0.1, 1.0, size=h)
+    stiff = rng.uniform(1.0, 10.0, size=h)
+    wq = rng.uniform(1.0, 10.0, size=nx)
+    wr = rng.uniform(0.01, 0.1, size=nu)
+    return Model(nx, nu, dt, P, damp, stiff, wq, wr, 10.0 * wq)
+
+
+def nmpc_tracking(model: Model, N: int, seed: int) -> Tracking:
+    """Start state ~ N(0, 0.5^2); joint-position targets a sin(w t + phi) with
+    matching velocity targets; initial guess = straight line from the start
+    to the final reference state, zero controls (not dynamically feasible)."""
+    nx, nu, h = model.nx, model.nu, model.nx // 2
+    rng = np.random.default_rng(seed)
+    xs = rng.normal(0.0, 0.5, size=nx)
+    amp = rng.uniform(0.2, 1.0, size=h)
+    w = rng.uniform(0.5, 3.0, size=h)
+    ph = rng.uniform(0.0, 2 * np.pi, size=h)
+    t = np.arange(N)[:, None] * model.dt
+    xref = np.concatenate([amp * np.sin(w * t + ph), amp * w * np.cos(w * t + ph)], axis=1)
+    s = np.linspace(0.0, 1.0, N)[:, None]
+    X = xs[None, :] + s * (xref[-1] - xs)[None, :]
+    U = np.zeros((max(N - 1, 0), nu))
+    return Tracking(N, xs, xref, X, U)
