@@ -294,6 +294,65 @@ int mpcg_backward_batched_noalloc(mpcg_handle *h, mpcg_dims dims, int B, const i
                                   const void *dx_bar, const void *du_bar, const mpcg_grads *grads,
                                   const mpcg_opts *opts, mpcg_stats *stats, void *stream);
 
+/* ---------------------------------------------------------------------
+ * The outer loop around the solve (Sec. II-A Steps 1 and 3, Sec. IV-C) on
+ * the library's synthetic model.  The paper linearises robot dynamics that
+ * are not part of this library; these calls use a Kuka-shaped stand-in so
+ * that a whole SQP iteration (linearise, form, precondition, solve,
+ * recover, line-search) runs on the device:
+ *   h = nx/2 joints, x = (p, v), u in R^nu (nu <= h),
+ *   v+ = v + dt (P u - damp * v - stiff * sin p),   p+ = p + dt v+,
+ *   l(x, u) = 1/2 sum wq (x - xref_k)^2 + 1/2 sum wr u^2 (stage),
+ *   l_f(x)  = 1/2 sum wf (x - xref_{N-1})^2 (terminal).
+ * Trajectories use the solve path's layouts: X[N][nx], U[N-1][nu],
+ * xref[N][nx]; batched calls add knot_off (as above) and xs[B][nx].
+ * nx <= 64, nu <= 32.
+ * --------------------------------------------------------------------- */
+typedef struct {
+    int nx, nu;
+    double dt;
+    const void *P;           /* [h][nu] input matrix */
+    const void *damp, *stiff; /* [h] */
+    const void *wq, *wr, *wf; /* [nx], [nu], [nx] diagonal cost weights */
+} mpcg_model;
+
+/* Writable LQ arrays (layouts of mpcg_lq). */
+typedef struct {
+    void *A, *B, *Qd, *Rd, *q, *r, *c;
+} mpcg_lq_out;
+
+/* Step 1 of Sec. II-A at the trajectory (X, U): A_k = df/dx, B_k = df/du,
+ * Qd_k = wq (wf at the last knot), Rd_k = wr, q_k = Qd_k (x_k - xref_k),
+ * r_k = wr u_k, c_0 = x_0 - x_s, c_{k+1} = x_{k+1} - f(x_k, u_k) (the c of
+ * Eq. KKT).  The outputs feed mpcg_form_schur as an mpcg_lq. */
+int mpcg_linearize(mpcg_handle *h, mpcg_dims dims, const mpcg_model *model, const void *X,
+                   const void *U, const void *xref, const void *xs, const mpcg_lq_out *out,
+                   void *stream);
+int mpcg_linearize_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
+                           const mpcg_model *model, const void *X, const void *U,
+                           const void *xref, const void *xs, const mpcg_lq_out *out,
+                           void *stream);
+
+/* Parallel line search (Sec. IV-C): for a = 0 .. n_alpha-1 (n_alpha <= 32)
+ * the L1 merit  J(X', U') + mu (||x'_0 - x_s||_1 + sum_k ||x'_{k+1} -
+ * f(x'_k, u'_k)||_1)  of (X', U') = (X, U) + 2^-a (dX, dU), evaluated in
+ * FP64 at the working-precision candidate points, is written to merit[b][a]
+ * (DEVICE double array, B x n_alpha); then every instance takes its
+ * smallest merit (merits within a relative 1e-11 of it count as ties; the
+ * longest tied step wins) and X, U are updated in
+ * place; alpha_index[b] (DEVICE int array, or NULL) receives the chosen a.
+ * mu > 0 is used as given; mu <= 0 takes mu_b = 1.1 max(1, ||lambda_b||_inf)
+ * from lambda (the multipliers of the solve that produced dX, dU). */
+int mpcg_line_search(mpcg_handle *h, mpcg_dims dims, const mpcg_model *model, void *X, void *U,
+                     const void *dX, const void *dU, const void *xref, const void *xs,
+                     const void *lambda, double mu, int n_alpha, double *merit, int *alpha_index,
+                     void *stream);
+int mpcg_line_search_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
+                             const mpcg_model *model, void *X, void *U, const void *dX,
+                             const void *dU, const void *xref, const void *xs,
+                             const void *lambda, double mu, int n_alpha, double *merit,
+                             int *alpha_index, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,11 +89,15 @@ def penalty(lam):
 
 def line_search(model, trk, X, U, dX, dU, mu, n_alpha=9):
     """Sec. IV-C: merits of (X, U) + a (dX, dU) for a in {1, 1/2, ...,
-    2^-(n_alpha-1)}; the smallest merit wins (the largest step on an exact
-    tie).  Returns (X', U', index, merits)."""
-    alphas = 0.5 ** np.arange(n_alpha)
+    2^-(n_alpha-1)}; the smallest merit wins, merits within a relative 1e-11
+    of it (below the rounding of their FP64 sums) count as ties, and the
+    longest tied step is taken.  Returns (X', U', index, merits)."""
+    X, U, dX, dU = (np.asarray(a) for a in (X, U, dX, dU))
+    t = X.dtype.type  # candidates are formed in the trajectory's own precision
+    alphas = [t(0.5 ** a) for a in range(n_alpha)]
     m = np.array([merit(model, trk, X + a * dX, U + a * dU, mu) for a in alphas])
-    i = int(np.argmin(m))
+    best = np.nanmin(m)
+    i = int(np.nonzero(m <= best + 1e-11 * abs(best))[0][0])
     return X + alphas[i] * dX, U + alphas[i] * dU, i, m
 
 

@@ -33,6 +33,7 @@ EXPORTS = (
     "mpcg_form_schur_batched", "mpcg_form_precon_batched", "mpcg_pcg_solve_batched",
     "mpcg_recover_step_batched", "mpcg_backward_batched", "mpcg_backward",
     "mpcg_backward_batched_noalloc", "mpcg_refine_step", "mpcg_refine_step_batched",
+    "mpcg_linearize", "mpcg_linearize_batched", "mpcg_line_search", "mpcg_line_search_batched",
 )
 
 
@@ -42,6 +43,15 @@ class mpcg_dims(C.Structure):
 
 class mpcg_lq(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("A", "B", "Qd", "Rd", "q", "r", "c", "Q", "R")]
+
+
+class mpcg_model(C.Structure):
+    _fields_ = [("nx", C.c_int), ("nu", C.c_int), ("dt", C.c_double)] + \
+        [(n, C.c_void_p) for n in ("P", "damp", "stiff", "wq", "wr", "wf")]
+
+
+class mpcg_lq_out(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("A", "B", "Qd", "Rd", "q", "r", "c")]
 
 
 class mpcg_schur(C.Structure):
@@ -123,6 +133,17 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.mpcg_backward_batched_noalloc.argtypes = [vp, mpcg_dims, i32, vp, P(mpcg_lq), P(mpcg_schur), vp,
                                                   vp, vp, vp, vp, vp, P(mpcg_grads), P(mpcg_opts), vp,
                                                   vp]
+    lib.mpcg_linearize.restype = i32
+    lib.mpcg_linearize.argtypes = [vp, mpcg_dims, P(mpcg_model), vp, vp, vp, vp, P(mpcg_lq_out), vp]
+    lib.mpcg_linearize_batched.restype = i32
+    lib.mpcg_linearize_batched.argtypes = [vp, mpcg_dims, i32, vp, P(mpcg_model), vp, vp, vp, vp,
+                                           P(mpcg_lq_out), vp]
+    lib.mpcg_line_search.restype = i32
+    lib.mpcg_line_search.argtypes = [vp, mpcg_dims, P(mpcg_model), vp, vp, vp, vp, vp, vp, vp,
+                                     C.c_double, i32, vp, vp, vp]
+    lib.mpcg_line_search_batched.restype = i32
+    lib.mpcg_line_search_batched.argtypes = [vp, mpcg_dims, i32, vp, P(mpcg_model), vp, vp, vp, vp,
+                                             vp, vp, vp, C.c_double, i32, vp, vp, vp]
     _lib = lib
     return lib
 

@@ -64,6 +64,9 @@ def test_line_search_picks_the_smallest_merit(prob):
     X2, U2, i, mer = nmpc.line_search(m, t, t.X, t.U, 8 * dX, 8 * dU, mu)
     ref = [nmpc.merit(m, t, t.X + a * 8 * dX, t.U + a * 8 * dU, mu) for a in 0.5 ** np.arange(9)]
     assert np.allclose(mer, ref, rtol=1e-15) and i == int(np.argmin(ref)) and i >= 2
+    # near-equal merits (within 1e-11 relative) resolve to the longest step
+    Xt, Ut, it, _ = nmpc.line_search(m, t, t.X, t.U, 0 * dX, 0 * dU, mu)
+    assert it == 0
     assert np.allclose(X2, t.X + 0.5 ** i * 8 * dX)
 
 
