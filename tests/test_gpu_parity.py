@@ -242,3 +242,23 @@ def test_precon_value_is_checked():
     from paper_2309_08079_gb300._lib import MPCGError
     with pytest.raises(MPCGError):
         run_gpu(gen.kuka_lq(14, 7, 16, 1).astype(np.float32), opts=make_opts(precon=2))
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_status_breakdown_on_an_indefinite_operator(mode):
+    """S+ replaced by -S+ after formation (Phi^-1 kept SPD): the first
+    p^T S p is negative, so every kernel form stops with MPCG_BREAKDOWN after
+    one iteration and leaves lambda finite."""
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    s = solver()
+    lt = LQTensors.from_numpy(gen.kuka_lq(14, 7, 48, 5).astype(np.float32))
+    sch = s.alloc_schur(lt)
+    s.form_schur(lt, sch)
+    s.form_precon(lt, sch)
+    sch.Sd.neg_()
+    sch.So.neg_()
+    lam = torch.zeros(48, 14, device="cuda")
+    st = read_stats(s.pcg_solve(lt, sch, lam, make_opts(mode=mode)))
+    assert st["status"][0] == 2 and st["iters"][0] == 1, st
+    assert torch.isfinite(lam).all()
