@@ -103,13 +103,17 @@ typedef struct {
     int max_iter;  /* <= 0: 10 N nx */
     int cluster;   /* CTAs per instance (1..16); 0 = automatic */
     int mode;      /* PCG kernel: 0 automatic; 1 a thread-block cluster per instance
-                      (matrices held on chip; the automatic choice whenever the
-                      horizon fits); 2 one CTA per instance reading the blocks
-                      from L2 (many instances at once, any horizon that fits
-                      shared memory; the automatic choice beyond a cluster);
-                      3 one CTA per instance with the blocks staged into shared
-                      memory by TMA bulk copies (needs 16-byte multiples and
-                      16-byte-aligned block arrays, else as 2) */
+                      (matrices held on chip, in registers for float32 nx = 14;
+                      the automatic choice whenever the horizon fits); 2 one CTA
+                      per instance reading the blocks from L2 (many instances at
+                      once, any horizon that fits shared memory; the automatic
+                      choice beyond a cluster); 3 one CTA per instance streaming
+                      each knot's blocks through shared memory as TMA tiles
+                      (even nx and 16-byte-aligned block arrays, else as 2);
+                      4 a cluster per instance with the matrices staged in
+                      shared memory, 8 lanes x 2 rows per knot and up to 64
+                      knots per CTA (nx <= 16): half the SMs per instance of
+                      mode 1, for throughput */
     /* Batched PCG only: solve just the instances listed (a DEVICE int
        array of n_instances distinct indices into the batch); NULL solves
        all B.  With a list, dims.N may be the largest horizon among the

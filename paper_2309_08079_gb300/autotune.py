@@ -63,7 +63,8 @@ def candidate_plans(Ns: np.ndarray) -> Dict[str, List[dict]]:
     group's longest horizon needs)."""
     edges = horizon_classes(Ns)
     one = lambda mode: [{"lo": 0, "hi": INF, "mode": mode, "cluster": 0}]
-    plans = {"single_auto": one(0), "single_cta_l2": one(2), "single_cta_tma": one(3)}
+    plans = {"single_auto": one(0), "single_cta_l2": one(2), "single_cta_tma": one(3),
+             "single_wide": one(4)}
     if len(edges) > 1:
         lo = [0] + edges[:-1]
         plans["classes_auto"] = [{"lo": a, "hi": b, "mode": 0, "cluster": 0}
@@ -80,6 +81,8 @@ def candidate_plans(Ns: np.ndarray) -> Dict[str, List[dict]]:
         plans["classes_cta_l2"] = [{"lo": a, "hi": b, "mode": 2, "cluster": 0}
                                    for a, b in zip(lo, edges)]
         plans["classes_tile"] = [{"lo": a, "hi": b, "mode": 3, "cluster": 0}
+                                 for a, b in zip(lo, edges)]
+        plans["classes_wide"] = [{"lo": a, "hi": b, "mode": 4, "cluster": 0}
                                  for a, b in zip(lo, edges)]
         # finer knots-per-CTA tiling: clusters of ceil(hi / kpc) CTAs holding
         # kpc knots each, so a smaller CTA shares its SM with another

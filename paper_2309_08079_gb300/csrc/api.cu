@@ -117,14 +117,20 @@ int choose_pcg_tile(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_schur 
     return MPCG_OK;
 }
 
-// Launch shape of the cluster PCG kernel for horizons up to Nmax.
+// Launch shape of the cluster PCG kernel for horizons up to Nmax.  `wide`
+// (opts.mode = 4, nx <= 16): operators staged in shared memory, 8 lanes x 2
+// rows per knot, up to 64 knots per CTA -- half the SMs per instance of the
+// register-resident form, for throughput.
 template <typename T>
-int choose_pcg_cluster(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, PcgLaunch &L) {
+int choose_pcg_cluster(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, PcgLaunch &L,
+                       bool wide = false) {
     L.cta_mode = 0;
     const int nx = d.nx;
-    const bool reg = std::is_same<T, float>::value && nx == 14;
+    if (wide && nx > 16) return MPCG_EUNSUPPORTED;
+    const bool reg = !wide && std::is_same<T, float>::value && nx == 14;
     int max_threads = kMaxThreads;
     if (reg) { L.lpk = 8; L.rpt = 2; max_threads = 256; }  // 2 register-resident rows per thread
+    else if (wide) { L.lpk = 8; L.rpt = 2; }
     else if (nx <= 16) { L.lpk = 16; L.rpt = 1; }
     else if (nx <= 32) { L.lpk = 32; L.rpt = 1; }
     else if (nx <= 64) { L.lpk = 32; L.rpt = 2; }
@@ -174,6 +180,7 @@ int choose_pcg(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, co
         return choose_pcg_cta<T>(h, d, B, L);
     }
     if (mode == 1) return choose_pcg_cluster<T>(h, d, B, o, L);
+    if (mode == 4) return choose_pcg_cluster<T>(h, d, B, o, L, true);
     int rc = choose_pcg_cluster<T>(h, d, B, o, L);
     if (rc == MPCG_EUNSUPPORTED && !(o && o->cluster > 0)) return choose_pcg_cta<T>(h, d, B, L);
     return rc;

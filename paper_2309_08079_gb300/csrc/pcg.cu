@@ -628,6 +628,7 @@ static void (*pcg_fn(const PcgLaunch &L))(const PcgParams<T>) {
     if constexpr (sizeof(T) == 4) {
         if (L.mode == MODE_REG) return pcg_cluster_kernel<float, MODE_REG, 8, 2>;
     }
+    if (L.lpk == 8) return pcg_cluster_kernel<T, MODE_PTR, 8, 2>;
     if (L.lpk == 16) return pcg_cluster_kernel<T, MODE_PTR, 16, 1>;
     if (L.rpt == 1) return pcg_cluster_kernel<T, MODE_PTR, 32, 1>;
     return pcg_cluster_kernel<T, MODE_PTR, 32, 2>;
@@ -674,6 +675,8 @@ static cudaError_t prepare_one(void (*fn)(const PcgParams<T>), int smem_optin) {
 cudaError_t pcg_prepare(int smem_optin) {
     cudaError_t e;
     if ((e = prepare_one<float>(pcg_cluster_kernel<float, MODE_REG, 8, 2>, smem_optin))) return e;
+    if ((e = prepare_one<float>(pcg_cluster_kernel<float, MODE_PTR, 8, 2>, smem_optin))) return e;
+    if ((e = prepare_one<double>(pcg_cluster_kernel<double, MODE_PTR, 8, 2>, smem_optin))) return e;
     if ((e = prepare_one<float>(pcg_cluster_kernel<float, MODE_PTR, 16, 1>, smem_optin))) return e;
     if ((e = prepare_one<float>(pcg_cluster_kernel<float, MODE_PTR, 32, 1>, smem_optin))) return e;
     if ((e = prepare_one<float>(pcg_cluster_kernel<float, MODE_PTR, 32, 2>, smem_optin))) return e;

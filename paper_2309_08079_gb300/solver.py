@@ -118,7 +118,9 @@ def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0, mode=0, instances=Non
               precon=0) -> L.mpcg_opts:
     """mode: 0 automatic, 1 cluster per instance, 2 one CTA per instance
     reading blocks from L2, 3 one CTA per instance streaming TMA tiles (as 2
-    when blocks are not 16-byte multiples).  precon: 0 symmetric stair
+    when blocks are not 16-byte multiples), 4 cluster per instance with
+    shared-memory operators and up to 64 knots per CTA (nx <= 16).  precon:
+    0 symmetric stair
     (Sec. IV-A), 1 block Jacobi."""
     o = L.mpcg_opts(float(tol), int(tol_mode), int(max_iter), int(cluster), int(mode), None, 0,
                     int(precon))

@@ -34,7 +34,7 @@ def _check(batch, lam, dx, du, st, tol):
         assert e_lam < tol and e_dz < tol, (b, it.N, e_lam, e_dz)
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4])
 @pytest.mark.parametrize("Ns", [[1, 5, 32, 33, 100, 64], [512, 3, 257], [2] * 7])
 def test_batched_ragged_parity(Ns, mode):
     from paper_2309_08079_gb300.solver import make_opts
@@ -43,7 +43,7 @@ def test_batched_ragged_parity(Ns, mode):
     _check(batch, lam, dx, du, st, TOL_F32)
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4])
 def test_batched_queue_more_instances_than_clusters(mode):
     """300 instances: more than the co-resident clusters or CTAs, so the
     persistent grid drains the instance queue."""

@@ -262,3 +262,20 @@ def test_status_breakdown_on_an_indefinite_operator(mode):
     st = read_stats(s.pcg_solve(lt, sch, lam, make_opts(mode=mode)))
     assert st["status"][0] == 2 and st["iters"][0] == 1, st
     assert torch.isfinite(lam).all()
+
+
+# ------------------------------------------------------------------ wide cluster form (mode 4)
+@pytest.mark.parametrize("nx,nu,N,dtype", [(14, 7, 1, "float32"), (14, 7, 17, "float32"),
+                                           (14, 7, 100, "float32"), (14, 7, 512, "float32"),
+                                           (14, 7, 700, "float32"), (6, 3, 50, "float32"),
+                                           (14, 7, 300, "float64")])
+def test_wide_cluster_parity(nx, nu, N, dtype):
+    """opts.mode = 4: operators staged in shared memory, up to 64 knots per
+    CTA (700 knots fit an 11-CTA cluster)."""
+    from paper_2309_08079_gb300.solver import make_opts
+    lq = gen.kuka_lq(nx, nu, N, 900 + N + nx)
+    f32 = dtype == "float32"
+    e_lam, e_dz, st = parity(lq, dtype=dtype, opts=make_opts(mode=4, tol=1e-6 if f32 else 1e-13))
+    assert st["status"][0] == 0, st
+    bar = TOL_F32 if f32 else TOL_F64
+    assert e_lam < bar and e_dz < bar, (e_lam, e_dz)
