@@ -533,9 +533,17 @@ def run_batched(s, dev, solves):
             b.synchronize()
             times.append(a.elapsed_time(b))
         stb = np.concatenate([read_stats(x) for x in stats])
+        # PCG algorithmic bytes of all the graph's solves over the whole graph
+        # time (formation and recovery included in the time)
+        alg = float(np.sum(stb["iters"].astype(np.float64) * np.tile(Ns, solves))) * \
+            pcg_bytes_per_knot_iter(c["nx"])
+        hbm, note = hbm_peak()
         per_mode[name] = {"graph_ms": float(np.median(times)),
                           "converged": bool(np.all(stb["status"] == 0)),
-                          "mean_iters": float(np.mean(stb["iters"]))}
+                          "mean_iters": float(np.mean(stb["iters"])),
+                          "pcg_roofline": {"bound": "hbm",
+                                           "frac": alg / (float(np.median(times)) / 1e3) / 1e9 / hbm,
+                                           "peak_source": note}}
         del g
     best = min(per_mode, key=lambda k: per_mode[k]["graph_ms"])
     t_graph = per_mode[best]["graph_ms"] / 1e3
@@ -616,6 +624,10 @@ def run_backward(s, dev, reps=5):
             fwd_ms.append(tf)
             bwd_ms.append(tb)
     ok = bool(np.all(read_stats(bst)["status"] == 0))
+    hbm, note = hbm_peak()
+    it_f = read_stats(st)["iters"].astype(np.float64)
+    it_b = read_stats(bst)["iters"].astype(np.float64)
+    alg = float(np.sum(it_f + it_b)) * c["N"] * pcg_bytes_per_knot_iter(c["nx"])
     # gradient of instance 0 against the oracle's analytic gradient
     it0 = batch.items[0].astype(np.float64)
     l0, x0, u0 = oracle.kkt_solve(it0)
@@ -642,7 +654,9 @@ def run_backward(s, dev, reps=5):
     f, bw = float(np.median(fwd_ms)), float(np.median(bwd_ms))
     return {"workload": f"{c['B']} instances x N={c['N']} (nx={c['nx']}, nu={c['nu']}), loss sum ||dz||^2 + w^T lambda",
             "fwd_ms": f, "bwd_ms": bw, "bwd_over_fwd": bw / f, "loop_fwd_bwd_ms": t_loop,
-            "speedup_vs_loop": t_loop / (f + bw), "converged": ok, "grad_relerr_vs_oracle": gerr}
+            "speedup_vs_loop": t_loop / (f + bw), "converged": ok, "grad_relerr_vs_oracle": gerr,
+            "pcg_roofline": {"bound": "hbm", "note": "forward and adjoint PCG bytes over fwd + bwd time",
+                             "frac": alg / ((f + bw) / 1e3) / 1e9 / hbm, "peak_source": note}}
 
 
 def _step_timer(s, stream):
