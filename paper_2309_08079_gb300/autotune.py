@@ -76,6 +76,8 @@ def candidate_plans(Ns: np.ndarray) -> Dict[str, List[dict]]:
         plans["classes_cta_short"] = short + [
             {"lo": max(a, cut) if short else a, "hi": b, "mode": 0, "cluster": 0}
             for a, b in zip(lo, edges) if b > cut]
+        if short:
+            plans["classes_tile_short"] = [dict(short[0], mode=3)] + plans["classes_cta_short"][1:]
         # per-class launches of the CTA-per-instance kernels (each class's
         # shared vectors sized for its own longest horizon)
         plans["classes_cta_l2"] = [{"lo": a, "hi": b, "mode": 2, "cluster": 0}

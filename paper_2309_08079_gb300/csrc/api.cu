@@ -95,12 +95,14 @@ int choose_pcg_tile(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_schur 
     L.lpk = nx <= 16 ? 16 : 32;
     L.rpt = nx <= 32 ? 1 : 2;
     L.vw = (sizeof(T) == 4 && nx % 4 == 0) ? 4 : 2;
+    L.nxc = (sizeof(T) == 4 && (nx == 14 || nx == 36)) ? nx : 0;
     L.vs = nx <= 16 ? 16 : ceil_div(nx, 4) * 4;
     L.kpc_max = d.N;
     const int SW = 32 / L.lpk;
     const int ns_want = std::max(1, std::min(32, ceil_div(d.N, 4)));
     int bestW = 0, bestD = 0;
-    for (int W = std::min(16, ceil_div(ns_want, SW)); W >= 1 && !bestW; --W)
+    const int wmax = L.nxc == 36 ? 8 : 16;  // the nx = 36 form is compiled for <= 256 threads
+    for (int W = std::min(wmax, ceil_div(ns_want, SW)); W >= 1 && !bestW; --W)
         for (int dep = 2; dep >= 1; --dep)
             if (pcg_tile_smem_bytes<T>(d.N, L.vs, W, W * SW, nx, dep) <= (size_t)h->smem_optin) {
                 bestW = W;

@@ -51,6 +51,7 @@ struct PcgLaunch {
     int lpk, rpt, mode, stage, vs, kpc_max;
     int vw;        // pcg_tile_kernel: elements per shared-memory row load (2 or 4)
     int depth;     // pcg_tile_kernel: steps each knot stream copies ahead (1..4)
+    int nxc;       // pcg_tile_kernel: nx fixed at compile time (14, 36), else 0
     size_t smem;
 };
 

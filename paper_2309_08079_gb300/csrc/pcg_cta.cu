@@ -319,10 +319,42 @@ __device__ __forceinline__ void vload(const T *p, T (&o)[VW]) {
 // nullptr: none).  One pass over the columns feeds all three accumulators,
 // so the three dependency chains overlap; each accumulator still adds its
 // products in column order, as rowdot_ptr does.  nx % VW == 0.
-template <typename T, int VW, int RPT, int LPK>
-__device__ __forceinline__ void tile_rows(int nx, int li, const T *D, const T *Lt, const T *Lg,
+template <typename T, int VW, int RPT, int LPK, bool HL, bool HU>
+__device__ __forceinline__ void tile_cols(int nx, int j, int li, const bool (&ok)[RPT], const T *D,
+                                          const T *Lt, const T *U, const T *vprev, const T *vself,
+                                          const T *vnext, T (&a0)[RPT], T (&a1)[RPT], T (&a2)[RPT]) {
+    T xs[VW], xp[VW], xn[VW];
+    vload<T, VW>(vself + j, xs);
+    if (HL) vload<T, VW>(vprev + j, xp);
+    if (HU) vload<T, VW>(vnext + j, xn);
+#pragma unroll
+    for (int m = 0; m < RPT; ++m)
+        if (ok[m]) {
+            const int i = li + m * LPK;
+            T d[VW], l[VW];
+            vload<T, VW>(D + i * nx + j, d);
+            if (HL) vload<T, VW>(Lt + i * nx + j, l);
+#pragma unroll
+            for (int t = 0; t < VW; ++t) {
+                a0[m] = fma_rn(d[t], xs[t], a0[m]);
+                if (HL) a1[m] = fma_rn(l[t], xp[t], a1[m]);
+                if (HU) a2[m] = fma_rn(U[(j + t) * nx + i], xn[t], a2[m]);
+            }
+        }
+}
+
+// Rows li, li + LPK, ... (RPT of them; rows >= nx skipped) of one block row
+// of the tiles times the halo'd vector: D (by rows), the lower block from a
+// tile (Lt, by rows; nullptr: none or Lg), the upper block U (by columns;
+// nullptr: none).  One pass over the columns feeds all three accumulators,
+// so the three dependency chains overlap; each accumulator still adds its
+// products in column order, as rowdot_ptr does.  nx % VW == 0.  NXC > 0
+// fixes nx at compile time (the column loop unrolls completely).
+template <typename T, int VW, int RPT, int LPK, int NXC>
+__device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T *Lt, const T *Lg,
                                           const T *U, const T *vprev, const T *vself,
                                           const T *vnext, T (&y)[RPT]) {
+    const int nx = NXC > 0 ? NXC : nx_rt;
     T a0[RPT], a1[RPT], a2[RPT];
     bool ok[RPT];
 #pragma unroll
@@ -330,29 +362,24 @@ __device__ __forceinline__ void tile_rows(int nx, int li, const T *D, const T *L
         a0[m] = a1[m] = a2[m] = T(0);
         ok[m] = li + m * LPK < nx;
     }
-    // a missing block reads a zero row (its slot is never used for data)
-    const bool hasL = Lt != nullptr, hasU = U != nullptr;
+    auto sweep = [&](auto hl, auto hu) {
+        constexpr bool HL = decltype(hl)::value, HU = decltype(hu)::value;
+        if constexpr (NXC > 0) {
+#pragma unroll
+            for (int j = 0; j < NXC; j += VW)
+                tile_cols<T, VW, RPT, LPK, HL, HU>(nx, j, li, ok, D, Lt, U, vprev, vself, vnext, a0, a1, a2);
+        } else {
 #pragma unroll 2
-    for (int j = 0; j < nx; j += VW) {
-        T xs[VW], xp[VW], xn[VW];
-        vload<T, VW>(vself + j, xs);
-        vload<T, VW>(vprev + j, xp);
-        vload<T, VW>(vnext + j, xn);
-#pragma unroll
-        for (int m = 0; m < RPT; ++m)
-            if (ok[m]) {
-                const int i = li + m * LPK;
-                T d[VW], l[VW];
-                vload<T, VW>(D + i * nx + j, d);
-                if (hasL) vload<T, VW>(Lt + i * nx + j, l);
-#pragma unroll
-                for (int t = 0; t < VW; ++t) {
-                    a0[m] = fma_rn(d[t], xs[t], a0[m]);
-                    if (hasL) a1[m] = fma_rn(l[t], xp[t], a1[m]);
-                    if (hasU) a2[m] = fma_rn(U[(j + t) * nx + i], xn[t], a2[m]);
-                }
-            }
-    }
+            for (int j = 0; j < nx; j += VW)
+                tile_cols<T, VW, RPT, LPK, HL, HU>(nx, j, li, ok, D, Lt, U, vprev, vself, vnext, a0, a1, a2);
+        }
+    };
+    using Y = std::true_type;
+    using N = std::false_type;
+    if (Lt && U) sweep(Y{}, Y{});
+    else if (Lt) sweep(Y{}, N{});
+    else if (U) sweep(N{}, Y{});
+    else sweep(N{}, N{});
     if (Lg) {  // lower block of a stream's first knot, straight from global memory
 #pragma unroll
         for (int m = 0; m < RPT; ++m)
@@ -381,8 +408,14 @@ __device__ __forceinline__ T tile_resid(int nx, int i, T b, const T *D, const T 
     return AT::to_T(a);
 }
 
-template <typename T, int LPK, int RPT, int VW>
-__global__ void __launch_bounds__(512, 1) pcg_tile_kernel(const PcgParams<T> P) {
+// The nx = 36 form caps its CTA at 8 warps so each thread may use up to 255
+// registers (its unrolled column loop keeps 2 rows x 3 accumulators plus the
+// vector chunks live).
+template <int NXC>
+constexpr int tile_max_threads() { return NXC == 36 ? 256 : 512; }
+
+template <typename T, int LPK, int RPT, int VW, int NXC = 0>
+__global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(const PcgParams<T> P) {
     using AT = Acc<T>;
     using A = typename AT::type;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -394,7 +427,7 @@ __global__ void __launch_bounds__(512, 1) pcg_tile_kernel(const PcgParams<T> P) 
     const int s = warp * SW + lane / LPK;  // this lane's stream
     const int li = lane % LPK;
     const bool leader = li == 0;
-    const int nx = P.nx, vs = P.vs, nx2 = nx * nx;
+    const int nx = NXC > 0 ? NXC : P.nx, vs = P.vs, nx2 = nx * nx;
     const uint32_t nxb = (uint32_t)(nx2 * sizeof(T));
     const int depth = P.depth;       // steps copied ahead
     const int RD = depth + 1, RO = depth + 2, RM = depth + 1;  // ring sizes
@@ -546,7 +579,7 @@ __global__ void __launch_bounds__(512, 1) pcg_tile_kernel(const PcgParams<T> P) 
                         }
                     } else {
                         T y[RPT];
-                        tile_rows<T, VW, RPT, LPK>(nx, li, D, Lt, Lg, U, v + k * vs, v + (k + 1) * vs,
+                        tile_rows<T, VW, RPT, LPK, NXC>(nx, li, D, Lt, Lg, U, v + k * vs, v + (k + 1) * vs,
                                                    v + (k + 2) * vs, y);
 #pragma unroll
                         for (int m = 0; m < RPT; ++m) {
@@ -743,6 +776,9 @@ cudaError_t pcg_cta_prepare(int smem_optin) {
 template <typename T>
 static void (*pcg_tile_fn(const PcgLaunch &L))(const PcgParams<T>) {
     if constexpr (sizeof(T) == 4) {
+        // the measured shapes with nx fixed at compile time
+        if (L.nxc == 14) return pcg_tile_kernel<T, 16, 1, 2, 14>;
+        if (L.nxc == 36) return pcg_tile_kernel<T, 32, 2, 4, 36>;
         if (L.vw == 4) {
             if (L.lpk == 16) return pcg_tile_kernel<T, 16, 1, 4>;
             if (L.rpt == 1) return pcg_tile_kernel<T, 32, 1, 4>;
@@ -783,6 +819,8 @@ int pcg_tile_max_blocks(const PcgLaunch &L) {
 cudaError_t pcg_tile_prepare(int smem_optin) {
     cudaError_t e;
     const auto a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 16, 1, 2, 14>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 4, 36>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 16, 1, 4>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 1, 4>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 4>, a, smem_optin))) return e;
