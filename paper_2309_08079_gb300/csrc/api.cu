@@ -167,11 +167,11 @@ int choose_pcg_cluster(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opt
     }
 }
 
-// Kernel choice: a cluster per instance whenever the horizon fits one
-// (measured fastest for single solves and for the 256-instance ragged batch:
-// 5.8k solves/s vs 4.7k with one CTA per instance reading L2 and 2.8k with
-// TMA-staged blocks), one CTA per instance for horizons beyond what a 16-CTA
-// cluster holds, or when asked for.
+// Kernel choice (mode 0): a cluster per instance whenever the horizon fits
+// one (fastest for single solves; for float32 nx = 14 batches the
+// register-resident clusters match the tiled kernel), the tiled kernel for
+// larger batches of other shapes, one CTA per instance reading L2 for
+// horizons beyond both.
 template <typename T>
 int choose_pcg(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, const mpcg_schur *s,
                PcgLaunch &L) {
@@ -184,6 +184,18 @@ int choose_pcg(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, co
     if (mode == 1) return choose_pcg_cluster<T>(h, d, B, o, L);
     if (mode == 4) return choose_pcg_cluster<T>(h, d, B, o, L, true);
     int rc = choose_pcg_cluster<T>(h, d, B, o, L);
+    // A batch that needs more than one wave of clusters, with operators the
+    // cluster kernel cannot keep in registers (anything but float32 nx = 14),
+    // goes to the tiled kernel: measured 1.25 s vs 3.16 s per solve of the
+    // 1024-instance nx = 36 batch.
+    const bool reg = std::is_same<T, float>::value && d.nx == 14;
+    if (!reg && !(o && o->cluster > 0) && (rc != MPCG_OK || (long)B * L.C > h->sms)) {
+        PcgLaunch Lt{};
+        if (choose_pcg_tile<T>(h, d, B, s, Lt) == MPCG_OK) {
+            L = Lt;
+            return MPCG_OK;
+        }
+    }
     if (rc == MPCG_EUNSUPPORTED && !(o && o->cluster > 0)) return choose_pcg_cta<T>(h, d, B, L);
     return rc;
 }
