@@ -666,12 +666,27 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
                         break;
                     }
                     const T alpha = AT::div(eta_t, ups);
-                    for (int e = tid; e < Nb * nx; e += nthreads) {
-                        const int k = e / nx, i = e % nx;
-                        const int o = (k + 1) * vs + i;
-                        T *lp = &P.lam[(size_t)(k0 + k) * nx + i];
-                        *lp = fma_rn(alpha, vp[o], *lp);
-                        vr[o] = fma_rn(-alpha, vw[o], vr[o]);
+                    // lambda += alpha p in global memory: each thread's four
+                    // loads are issued before any store, so their latencies
+                    // overlap
+                    T *lam0 = P.lam + (size_t)k0 * nx;
+                    const int nel = Nb * nx;
+                    for (int e0 = tid; e0 < nel; e0 += 4 * nthreads) {
+                        T l[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int e = e0 + u * nthreads;
+                            l[u] = e < nel ? lam0[e] : T(0);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int e = e0 + u * nthreads;
+                            if (e < nel) {
+                                const int o = (e / nx + 1) * vs + e % nx;
+                                lam0[e] = fma_rn(alpha, vp[o], l[u]);
+                                vr[o] = fma_rn(-alpha, vw[o], vr[o]);
+                            }
+                        }
                     }
                     __syncthreads();
                     A s2 = AT::zero();
