@@ -355,12 +355,18 @@ __device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T
                                           const T *U, const T *vprev, const T *vself,
                                           const T *vnext, T (&y)[RPT]) {
     const int nx = NXC > 0 ? NXC : nx_rt;
+    // nx fixed a little above a warp (nx = 36): the 4 rows past the first 32
+    // are split over the whole warp, 8 lanes per row with a strided subset
+    // of the columns each and a 3-level shuffle sum, instead of a second
+    // pass in which 4 of 32 lanes work.  (These rows keep their own, equally
+    // valid, summation order.)
+    constexpr bool SPLIT = RPT == 2 && LPK == 32 && NXC > LPK && NXC - LPK <= 4;
     T a0[RPT], a1[RPT], a2[RPT];
     bool ok[RPT];
 #pragma unroll
     for (int m = 0; m < RPT; ++m) {
         a0[m] = a1[m] = a2[m] = T(0);
-        ok[m] = li + m * LPK < nx;
+        ok[m] = li + m * LPK < nx && !(SPLIT && m > 0);
     }
     auto sweep = [&](auto hl, auto hu) {
         constexpr bool HL = decltype(hl)::value, HU = decltype(hu)::value;
@@ -389,6 +395,26 @@ __device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T
     }
 #pragma unroll
     for (int m = 0; m < RPT; ++m) y[m] = (a0[m] + a1[m]) + a2[m];
+    if constexpr (SPLIT) {
+        const int row = LPK + (li >> 3), g = li & 7;
+        const bool live = row < NXC;
+        const T *Ls = Lt ? Lt : Lg;  // tile (shared) or global: generic loads
+        T t0 = T(0), t1 = T(0), t2 = T(0);
+#pragma unroll
+        for (int q = 0; q < (NXC + 7) / 8; ++q) {
+            const int j = g + 8 * q;
+            if (live && j < NXC) {
+                t0 = fma_rn(D[row * NXC + j], vself[j], t0);
+                if (Ls) t1 = fma_rn(Ls[row * NXC + j], vprev[j], t1);
+                if (U) t2 = fma_rn(U[j * NXC + row], vnext[j], t2);
+            }
+        }
+        T t = (t0 + t1) + t2;
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t += __shfl_xor_sync(0xffffffffu, t, 4);
+        y[1] = __shfl_sync(0xffffffffu, t, (li & 3) * 8);  // lanes 0..3: rows 32..35
+    }
 }
 
 // b_i - (row i) . v with exact products and an extended sum (as resid_ptr)
