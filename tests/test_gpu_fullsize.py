@@ -73,6 +73,33 @@ def test_batch256_full_size():
     _check_sample(batch, lam, dx, du, st, picks, TOL_F32, TOL_F32)
 
 
+@pytest.mark.parametrize("plan", ["single_cta_tma", "classes_auto"])
+def test_batch256_full_size_in_the_benchmark_plans(plan):
+    """The same batch through the launch plans the benchmark's autotuner
+    chooses between (the tiled kernel with a longest-first queue; per-class
+    clusters on forked streams)."""
+    import torch
+    from paper_2309_08079_gb300.autotune import PlanRunner, candidate_plans
+    from paper_2309_08079_gb300.solver import LQTensors, read_stats
+    c = gen.CONFIG_BATCH
+    Ns = gen.batch_horizons(c["B"], c["N_lo"], c["N_hi"], c["n_seed"])
+    batch = gen.kuka_batch(c["nx"], c["nu"], Ns, c["seed_base"], dt=c["dt"], qd=c["qd"]).astype(np.float32)
+    s = solver()
+    lt = LQTensors.from_batch(batch)
+    sch = s.alloc_schur(lt)
+    s.form_schur(lt, sch)
+    s.form_precon(lt, sch)
+    runner = PlanRunner(s, lt, candidate_plans(lt.Ns)[plan])
+    lam = torch.zeros(lt.total, lt.nx, device="cuda")
+    stats = s.alloc_stats(lt.nb)
+    runner.pcg_solve(sch, lam, stats)
+    dx, du = s.recover_step(lt, lam)
+    torch.cuda.synchronize()
+    picks = [int(np.argmin(Ns)), int(np.argmax(Ns))] + list(range(3, batch.B, 41))
+    _check_sample(batch, lam.cpu().double().numpy(), dx.cpu().double().numpy(),
+                  du.cpu().double().numpy(), read_stats(stats), picks, TOL_F32, TOL_F32)
+
+
 @pytest.mark.slow
 def test_large_state_batch_full_size():
     """nx = 36, nu = 12, 1024 instances with N_i ~ U{64..256}, dt = 0.005,
