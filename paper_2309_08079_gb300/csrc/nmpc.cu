@@ -17,7 +17,7 @@ namespace mpcg {
 namespace {
 
 constexpr int LIN_THREADS = 128;  // 4 knots per block, one warp each
-constexpr int MERIT_THREADS = 256;
+constexpr int MERIT_THREADS = 64;   // one knot per thread; a block per chunk of 64 knots
 constexpr int MAX_ALPHA = 32;
 
 template <typename T>
@@ -122,11 +122,14 @@ linearize_kernel(ModelView<T> m, BatchView bv, const T *__restrict__ X, const T 
 }
 
 // ---------------------------------------------------------------------------
-// merit: block (b, a) evaluates the L1 merit of (X, U) + alpha_a (dX, dU),
-// alpha_a = 2^-a, in FP64:  J + mu_b (||x'_0 - x_s||_1 + sum ||x'_{k+1} -
-// f(x'_k, u'_k)||_1).  The candidate point is rounded to the working type
-// first, as the applied step will be.  mu_b = mu when mu > 0, else
-// 1.1 max(1, max |lambda_b|).
+// merit: the L1 merit of (X, U) + alpha_a (dX, dU), alpha_a = 2^-a, in FP64:
+// J + mu_b (||x'_0 - x_s||_1 + sum ||x'_{k+1} - f(x'_k, u'_k)||_1).  The
+// candidate point is rounded to the working type first, as the applied step
+// will be.  mu_b = mu when mu > 0, else 1.1 max(1, max |lambda_b|).  Block
+// (b, a, chunk) takes 64 knots of instance b, one per thread, and adds its
+// share to merit[b][a] (zeroed before the launch) with an FP64 atomic: the
+// FP64 work spreads over many SMs, and the summation order only moves the
+// merits by rounding, far below the tie tolerance of the choice.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -163,19 +166,30 @@ merit_kernel(ModelView<T> m, BatchView bv, int n_alpha, const T *__restrict__ X,
     if (b >= bv.B) return;
     int k0, Nb;
     bv.range(b, k0, Nb);
+    const int kbase = blockIdx.y * MERIT_THREADS;
+    if (kbase >= Nb) return;  // whole block: this instance is shorter
     const int c0 = k0 - b;
     const int nx = m.nx, nu = m.nu;
     const T alpha = T(ldexp(1.0, -a));
     double mub = mu;
     if (!(mu > 0.0)) {
-        double mx = 0.0;
-        for (int e = threadIdx.x; e < Nb * nx; e += blockDim.x)
-            mx = fmax(mx, fabs((double)lam[(size_t)k0 * nx + e]));
-        mub = 1.1 * fmax(1.0, block_max<T>(mx, red));
+        // max |lambda_b|: eight independent loads per thread in flight
+        const T *lb = lam + (size_t)k0 * nx;
+        const int n = Nb * nx, step = blockDim.x;
+        T mx = T(0);
+        for (int e0 = threadIdx.x; e0 < n; e0 += 8 * step) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = e0 + u * step < n ? lb[e0 + u * step] : T(0);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) mx = fmax(mx, fabs(v[u]));
+        }
+        mub = 1.1 * fmax(1.0, block_max<T>((double)mx, red));
     }
     double J = 0.0, viol = 0.0;
-    T xp[64], up[32], xk[64];  // candidate x'_{k-1}, u'_{k-1}, x'_k (nx <= 64, nu <= 32)
-    for (int k = threadIdx.x; k < Nb; k += blockDim.x) {
+    const int k = kbase + threadIdx.x;
+    if (k < Nb) {
+        T xp[64], up[32], xk[64];  // candidate x'_{k-1}, u'_{k-1}, x'_k (nx <= 64, nu <= 32)
         const size_t o = (size_t)(k0 + k) * nx;
         const bool last = k + 1 >= Nb;
         for (int i = 0; i < nx; ++i) {
@@ -195,12 +209,16 @@ merit_kernel(ModelView<T> m, BatchView bv, int n_alpha, const T *__restrict__ X,
             for (int i = 0; i < nx; ++i) xp[i] = X[op + i] + alpha * dX[op + i];
             for (int i = 0; i < nu; ++i)
                 up[i] = U[(size_t)(c0 + k - 1) * nu + i] + alpha * dU[(size_t)(c0 + k - 1) * nu + i];
-            for (int i = 0; i < nx; ++i) viol += fabs((double)xk[i] - fdyn<T, double>(m, i, xp, up));
+            // each joint's velocity update once, then both of its rows
+            for (int i = 0; i < m.h; ++i) {
+                const double vn = vnext<T, double>(m, i, xp, up);
+                viol += fabs((double)xk[i] - ((double)xp[i] + m.dt * vn));
+                viol += fabs((double)xk[m.h + i] - vn);
+            }
         }
     }
-    J = block_sum<T>(J, red);
-    viol = block_sum<T>(viol, red);
-    if (threadIdx.x == 0) merit[(size_t)b * n_alpha + a] = J + mub * viol;
+    const double part = block_sum<T>(J + mub * viol, red);
+    if (threadIdx.x == 0) atomicAdd(&merit[(size_t)b * n_alpha + a], part);
 }
 
 // ---------------------------------------------------------------------------
@@ -295,10 +313,13 @@ int line_search_t(const mpcg_dims &d, int B, const int *knot_off, const mpcg_mod
                   const void *lam, double mu, int n_alpha, double *merit, int *alpha_index,
                   cudaStream_t st) {
     const BatchView bv = bview(knot_off, B, d.N);
-    merit_kernel<T><<<B * n_alpha, MERIT_THREADS, 0, st>>>(
+    int rc = err(cudaMemsetAsync(merit, 0, sizeof(double) * (size_t)B * n_alpha, st));
+    if (rc) return rc;
+    const dim3 grid(B * n_alpha, (d.N + MERIT_THREADS - 1) / MERIT_THREADS);
+    merit_kernel<T><<<grid, MERIT_THREADS, 0, st>>>(
         view<T>(m), bv, n_alpha, (const T *)X, (const T *)U, (const T *)dX, (const T *)dU,
         (const T *)xref, (const T *)xs, (const T *)lam, mu, merit);
-    int rc = err(cudaGetLastError());
+    rc = err(cudaGetLastError());
     if (rc) return rc;
     const int K = knot_off ? B * d.N : d.N;
     const int per = LIN_THREADS / 32;
