@@ -5,8 +5,8 @@ Workload: the latency sweep's largest single instance -- seeded Kuka-shaped
 LQ data, nx = 14, nu = 7, N = 512 knot points, float32 storage with
 extended-precision dot products, PCG warm-started from the previous solution
 perturbed by 1% relative N(0, 1) noise, exit at relative residual 1e-6.
-One step = one whole pass of the path: form_schur, form_precon, pcg_solve,
-recover_step.  L2 is flushed (a 256 MiB write) between timed steps; steps
+One step = one whole pass of the path: form_schur and form_precon (one fused
+launch), pcg_solve, recover_step.  L2 is flushed (a 256 MiB write) between timed steps; steps
 are timed on the device with CUDA events on the launching stream.
 
 Also measured in the same run and reported in the same JSON line:
@@ -300,8 +300,7 @@ def run_ours(args, rank, world, local_rank):
     def step(i):
         e = ev[i]
         e[0].record(stream)
-        s.form_schur(lt, sch)
-        s.form_precon(lt, sch)
+        s.form(lt, sch)
         e[1].record(stream)
         s.pcg_solve(lt, sch, lam_bufs[i], opts, stats[i * 24:(i + 1) * 24])
         e[2].record(stream)
@@ -404,7 +403,7 @@ def run_ours(args, rank, world, local_rank):
                       "cold": int(cold["iters"])},
         "converged": converged,
         "parity": {"err_lambda": err_lam, "err_dz": err_dz, "tol": 1e-4},
-        "clocks": clk, "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roofline,
+        "clocks": clk, "e2e": e2e, "gpu_launches": 3 * args.steps, "roofline": roofline,
         "cpu_baseline": cpu, "batched": batched, "backward": backward, "sweep": sweep,
         "exit_sweep": exit_sweep, "precon_compare": precon_compare, "dense_cost": dense_cost,
         "nmpc": nmpc,
@@ -444,8 +443,7 @@ def run_e2e(s, lq, lam0, opts, dev, flush, steps, warmup):
         for f in LQTensors.FIELDS:
             getattr(lt, f).copy_(host[f], non_blocking=True)
         lam_d.copy_(lam_h[i], non_blocking=True)
-        s.form_schur(lt, sch)
-        s.form_precon(lt, sch)
+        s.form(lt, sch)
         s.pcg_solve(lt, sch, lam_d, opts, stats)
         s.recover_step(lt, lam_d, dx_d, du_d)
         out_lam.copy_(lam_d, non_blocking=True)
@@ -492,8 +490,7 @@ def run_batched(s, dev, solves):
 
     def body(opts_m):
         for r in range(solves):
-            s.form_schur(lt, sch)
-            s.form_precon(lt, sch)
+            s.form(lt, sch)
             if isinstance(opts_m, PlanRunner):
                 opts_m.pcg_solve(sch, work[r], stats[r])
             else:
@@ -562,8 +559,7 @@ def run_batched(s, dev, solves):
     for r in range(solves):
         for bi, it in enumerate(items):
             lam_i = work[r][ko[bi]:ko[bi + 1]]
-            s.form_schur(it, schs[bi])
-            s.form_precon(it, schs[bi])
+            s.form(it, schs[bi])
             s.pcg_solve(it, schs[bi], lam_i, opts, st1)
             s.recover_step(it, lam_i)
     b.record()
@@ -682,8 +678,8 @@ def _step_timer(s, stream):
 def run_sweep(s, dev, reps, flush):
     """Latency sweep: single instances at N in {64, 128, 256, 512}, each
     solved `reps` times warm-started from its converged lambda perturbed
-    (seed 2 + N, repetition r); one solve = form_schur, form_precon,
-    pcg_solve, recover_step, L2 flushed before each."""
+    (seed 2 + N, repetition r); one solve = the fused form_schur +
+    form_precon, pcg_solve, recover_step, L2 flushed before each."""
     import torch
     from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
     c = gen.CONFIG_SWEEP
@@ -705,15 +701,13 @@ def run_sweep(s, dev, reps, flush):
         tim, pcg = _step_timer(s, stream), _step_timer(s, stream)
 
         def one(r):
-            s.form_schur(lt, sch)
-            s.form_precon(lt, sch)
+            s.form(lt, sch)
             pcg(lambda: s.pcg_solve(lt, sch, lams[r], opts, stats[r * 24:(r + 1) * 24]))
             s.recover_step(lt, lams[r], dx, du)
 
         for r in range(min(3, reps)):  # warm-up on copies
             w = lams[r].clone()
-            s.form_schur(lt, sch)
-            s.form_precon(lt, sch)
+            s.form(lt, sch)
             s.pcg_solve(lt, sch, w, opts)
         torch.cuda.synchronize()
         for r in range(reps):
@@ -842,7 +836,7 @@ def run_dense_cost(s, dev, reps):
 
             def one():
                 lam.zero_()
-                frm(lambda: (s.form_schur(lt, sch), s.form_precon(lt, sch)))
+                frm(lambda: s.form(lt, sch))
                 s.pcg_solve(lt, sch, lam, o, st)
                 s.recover_step(lt, lam, dx, du)
 
@@ -854,7 +848,7 @@ def run_dense_cost(s, dev, reps):
                                                  du[:N - 1].cpu().double().numpy().ravel()]),
                                  np.concatenate([xo.ravel(), uo.ravel()]))
             out[f"N{N}_{name}"] = {"us_per_solve": pct(np.array(tim.ms()) * 1e3),
-                                   "form_precon_us": float(np.median(frm.ms())) * 1e3,
+                                   "form_us": float(np.median(frm.ms())) * 1e3,
                                    "iters": int(read_stats(st)["iters"][0]),
                                    "converged": bool(read_stats(st)["status"][0] == 0),
                                    "err_lambda": e_lam, "err_dz": e_dz}
@@ -932,8 +926,7 @@ def run_large(s, dev, solves, B=None):
     base = make_opts(tol=1e-6)
     sch = s.alloc_schur(lt)
     ws = s.alloc_workspace(lt)
-    s.form_schur(lt, sch)
-    s.form_precon(lt, sch)
+    s.form(lt, sch)
     zero = torch.zeros(lt.total, lt.nx, device=dev)
     with tempfile.TemporaryDirectory() as td:
         tuner = Autotuner(s, cache_path=os.path.join(td, "tune.json"), reps=1)

@@ -179,6 +179,21 @@ int mpcg_form_schur(mpcg_handle *h, mpcg_dims dims, const mpcg_lq *lq, mpcg_schu
 int mpcg_form_precon(mpcg_handle *h, mpcg_dims dims, mpcg_schur *schur, void *stream);
 
 /*
+ * mpcg_form_schur followed by mpcg_form_precon in one launch (nx <= 16): one
+ * warp per knot k forms block row k of S+, gamma_k and Pd[k]; a CTA takes
+ * consecutive knots and one extra warp that forms D_{k+1} and phi_k of the
+ * knot after its last, so that Po[k] = -Pd[k+1] phi_k Pd[k] is formed from
+ * shared memory.  The outputs are those of the two calls up to rounding
+ * (the same formulas in the same order; ~1 ulp per entry where the compiler
+ * contracts other multiply-adds).
+ * Dense cost blocks (lq->Q) and nx > 16 take the two calls' route.  Same
+ * arguments and errors as mpcg_form_schur; schur->Pd and schur->Po are
+ * required.
+ */
+int mpcg_form_schur_precon(mpcg_handle *h, mpcg_dims dims, const mpcg_lq *lq, mpcg_schur *schur,
+                           void *stream);
+
+/*
  * PCG (Algorithm 1) on S+ lambda = -gamma with preconditioner Phi^-1, in one
  * persistent launch.  `lambda` is read as the warm start lambda_0 and
  * overwritten with the result.  `stats` is a DEVICE pointer (one entry)
@@ -229,6 +244,8 @@ int mpcg_form_schur_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *kn
                             const mpcg_lq *lq, mpcg_schur *schur, void *stream);
 int mpcg_form_precon_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
                              mpcg_schur *schur, void *stream);
+int mpcg_form_schur_precon_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
+                                   const mpcg_lq *lq, mpcg_schur *schur, void *stream);
 int mpcg_pcg_solve_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *knot_off,
                            const mpcg_schur *schur, void *lambda, const mpcg_opts *opts,
                            mpcg_stats *stats, void *workspace, void *stream);

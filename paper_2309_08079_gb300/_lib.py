@@ -34,6 +34,7 @@ EXPORTS = (
     "mpcg_recover_step_batched", "mpcg_backward_batched", "mpcg_backward",
     "mpcg_backward_batched_noalloc", "mpcg_refine_step", "mpcg_refine_step_batched",
     "mpcg_linearize", "mpcg_linearize_batched", "mpcg_line_search", "mpcg_line_search_batched",
+    "mpcg_form_schur_precon", "mpcg_form_schur_precon_batched",
 )
 
 
@@ -133,6 +134,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.mpcg_backward_batched_noalloc.argtypes = [vp, mpcg_dims, i32, vp, P(mpcg_lq), P(mpcg_schur), vp,
                                                   vp, vp, vp, vp, vp, P(mpcg_grads), P(mpcg_opts), vp,
                                                   vp]
+    lib.mpcg_form_schur_precon.restype = i32
+    lib.mpcg_form_schur_precon.argtypes = [vp, mpcg_dims, P(mpcg_lq), P(mpcg_schur), vp]
+    lib.mpcg_form_schur_precon_batched.restype = i32
+    lib.mpcg_form_schur_precon_batched.argtypes = [vp, mpcg_dims, i32, vp, P(mpcg_lq), P(mpcg_schur), vp]
     lib.mpcg_linearize.restype = i32
     lib.mpcg_linearize.argtypes = [vp, mpcg_dims, P(mpcg_model), vp, vp, vp, vp, P(mpcg_lq_out), vp]
     lib.mpcg_linearize_batched.restype = i32

@@ -1,6 +1,6 @@
 """torch.autograd.Function around the solve path (no counterpart in the paper).
 
-Forward runs form_schur, form_precon, pcg_solve and recover_step; it saves
+Forward runs the fused form_schur + form_precon, pcg_solve and recover_step; it saves
 only S+, Phi^-1 (Sd, So, Pd, Po) and the solution (lambda, dx, du) besides
 the inputs.  Backward runs the library's adjoint: a second PCG solve on the
 same S+ with the same preconditioner, then per-knot outer products (see

@@ -11,6 +11,12 @@
 
 #include "launch.cuh"
 
+namespace mpcg {
+// fused formation (csrc/form.cu): S+, gamma, Pd, Po in one launch
+template <typename T> cudaError_t launch_form_fused(const SchurArgs<T> &, T *Pd, T *Po, int sms,
+                                                    cudaStream_t);
+template <typename T> size_t form_fused_smem_bytes(int nx, int nu, int Kgrid, int sms);
+}  // namespace mpcg
 
 using namespace mpcg;
 
@@ -302,11 +308,47 @@ int backward_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, c
                                    (T *)g->c, st));
 }
 
+// Formation of S+, gamma and Phi^-1 in one launch (diagonal costs); dense
+// cost blocks take the two-call route.
+template <typename T>
+int form_all_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const mpcg_lq *lq,
+               mpcg_schur *s, cudaStream_t st);
+
 template <typename T>
 int precon_t(const mpcg_dims &d, int B, const int *knot_off, mpcg_schur *s, cudaStream_t st) {
     return err_cuda(launch_form_precon<T>(d.nx, make_bv(knot_off, B, d.N), knot_off ? B * d.N : d.N,
                                           (const T *)s->Sd, (const T *)s->So, (T *)s->Pd,
                                           (T *)s->Po, st));
+}
+
+template <typename T>
+int form_all_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const mpcg_lq *lq,
+               mpcg_schur *s, cudaStream_t st) {
+    // Dense costs, and nx > 16 (one CTA per knot, where repeating D_{k+1}'s
+    // formation and inversion in every CTA costs more than the two launches
+    // it saves): the two separate launches.
+    const int Kgrid = knot_off ? B * d.N : d.N;
+    if (lq->Q || d.nx > 16 || form_fused_smem_bytes<T>(d.nx, d.nu, Kgrid, h->sms) > (size_t)h->smem_optin) {
+        int rc = form_schur_t<T>(h, d, B, knot_off, lq, s, st);
+        return rc ? rc : precon_t<T>(d, B, knot_off, s, st);
+    }
+    SchurArgs<T> a;
+    a.nx = d.nx;
+    a.nu = d.nu;
+    a.bv = make_bv(knot_off, B, d.N);
+    a.Kgrid = Kgrid;
+    a.A = (const T *)lq->A; a.B = (const T *)lq->B; a.Qd = (const T *)lq->Qd;
+    a.Rd = (const T *)lq->Rd; a.q = (const T *)lq->q; a.r = (const T *)lq->r;
+    a.c = (const T *)lq->c;
+    a.Qf = nullptr;
+    a.Rf = nullptr;
+    a.Sd = (T *)s->Sd; a.So = (T *)s->So; a.gamma = (T *)s->gamma;
+    a.info = s->info;
+    if (s->info) {
+        int e = err_cuda(cudaMemsetAsync(s->info, 0, sizeof(unsigned) * B, st));
+        if (e) return e;
+    }
+    return err_cuda(launch_form_fused<T>(a, (T *)s->Pd, (T *)s->Po, h->sms, st));
 }
 
 template <typename T>
@@ -428,6 +470,19 @@ int mpcg_form_schur_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_
 
 int mpcg_form_schur(mpcg_handle *h, mpcg_dims d, const mpcg_lq *lq, mpcg_schur *s, void *stream) {
     return mpcg_form_schur_batched(h, d, 1, nullptr, lq, s, stream);
+}
+
+int mpcg_form_schur_precon_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,
+                                   const mpcg_lq *lq, mpcg_schur *s, void *stream) {
+    if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !s->Sd ||
+        !s->Pd || !s->gamma || (d.N > 1 && (!s->So || !s->Po)))
+        return MPCG_EINVAL;
+    return DISPATCH(d, form_all_t, h, d, B, knot_off, lq, s, (cudaStream_t)stream);
+}
+
+int mpcg_form_schur_precon(mpcg_handle *h, mpcg_dims d, const mpcg_lq *lq, mpcg_schur *s,
+                           void *stream) {
+    return mpcg_form_schur_precon_batched(h, d, 1, nullptr, lq, s, stream);
 }
 
 int mpcg_form_precon_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off, mpcg_schur *s,

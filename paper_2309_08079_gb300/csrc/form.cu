@@ -422,6 +422,202 @@ __global__ void axpy_kernel(int nx, BatchView bv, const T *__restrict__ d, T *__
 }
 
 // ---------------------------------------------------------------------------
+// Fused formation (diagonal costs): block row k of S+ and gamma_k (as
+// form_schur_kernel), Pd[k] = D_k^-1 (as precon_inv_kernel) and, when k has
+// a successor, Po[k] = -Pd[k+1] phi_k Pd[k] (as precon_off_kernel) in one
+// launch, with no round trip through memory for the intermediate blocks.
+// The operations and their order are those of the three kernels; the values
+// agree with theirs to rounding (compile-time loop shapes let the compiler
+// contract other multiply-adds).
+// ---------------------------------------------------------------------------
+// NXC, NUC: compile-time nx, nu (0: taken from the arguments at run time).
+template <typename T, int NXC, int NUC>
+__device__ __forceinline__ void row_blocks(const SchurArgs<T> &a, int t, int kgrow, int j,
+                                           T *Am, T *As, T *Bm, T *Bs, T *iq0, T *iq1, T *qs,
+                                           T *ir, T *rs, T *q1, T *D, bool &bad) {
+    // theta for row kgrow (> instance start): D = A Q^-1 A^T + B R^-1 B^T + Q+^-1,
+    // As = A Q^-1 (so phi = -As); qs = Q^-1 q, rs = R^-1 r, q1 = q+
+    constexpr int G = 32;
+    const int nx = NXC ? NXC : a.nx, nu = NUC ? NUC : a.nu;
+    for (int i = t; i < nx; i += G) {
+        T v = a.Qd[(size_t)kgrow * nx + i];
+        bad |= !good_weight(v);
+        iq1[i] = T(1) / v;
+        q1[i] = a.q[(size_t)kgrow * nx + i];
+        v = a.Qd[(size_t)(kgrow - 1) * nx + i];
+        bad |= !good_weight(v);
+        iq0[i] = T(1) / v;
+        qs[i] = a.q[(size_t)(kgrow - 1) * nx + i] / v;
+    }
+    for (int i = t; i < nu; i += G) {
+        T v = a.Rd[(size_t)j * nu + i];
+        bad |= !good_weight(v);
+        ir[i] = T(1) / v;
+        rs[i] = a.r[(size_t)j * nu + i] / v;
+    }
+    group_sync(G);
+    const T *Ak = a.A + (size_t)j * nx * nx;
+    const T *Bk = a.B + (size_t)j * nx * nu;
+    for (int e = t; e < nx * nx; e += G) {
+        T v = Ak[e];
+        Am[e] = v;
+        As[e] = v * iq0[e % nx];
+    }
+    for (int e = t; e < nx * nu; e += G) {
+        T v = Bk[e];
+        Bm[e] = v;
+        Bs[e] = v * ir[e % nu];
+    }
+    group_sync(G);
+    for (int e = t; e < nx * nx; e += G) {
+        const int i = e / nx, jj = e % nx;
+        if (i > jj) continue;
+        T s = T(0);
+        for (int m = 0; m < nx; ++m) s += As[i * nx + m] * Am[jj * nx + m];
+        for (int m = 0; m < nu; ++m) s += Bs[i * nu + m] * Bm[jj * nu + m];
+        if (i == jj) s += iq1[i];
+        D[i * nx + jj] = s;
+        D[jj * nx + i] = s;
+    }
+    group_sync(G);
+}
+
+// Gauss-Jordan inverse of the SPD block M in place, then M <- (M + M^T)/2 into
+// out (the operations of precon_inv_kernel).
+template <typename T, int NXC>
+__device__ __forceinline__ void gj_inverse_sym(T *M, T *out, int nx_rt, int t) {
+    constexpr int G = 32;
+    const int nx = NXC ? NXC : nx_rt;
+    for (int j = 0; j < nx; ++j) {
+        const T d = T(1) / M[j * nx + j];
+        for (int c = t; c < nx; c += G)
+            if (c != j) M[j * nx + c] *= d;
+        group_sync(G);
+        const int n1 = nx - 1;
+        for (int e = t; e < n1 * n1; e += G) {
+            int i = e / n1, c = e % n1;
+            i += (i >= j);
+            c += (c >= j);
+            M[i * nx + c] -= M[i * nx + j] * M[j * nx + c];
+        }
+        group_sync(G);
+        for (int i = t; i < nx; i += G) {
+            if (i != j) M[i * nx + j] = -M[i * nx + j] * d;
+            else M[j * nx + j] = d;
+        }
+        group_sync(G);
+    }
+    for (int e = t; e < nx * nx; e += G) {
+        int i = e / nx, c = e % nx;
+        out[e] = T(0.5) * (M[i * nx + c] + M[c * nx + i]);
+    }
+    group_sync(G);
+}
+
+// Warp form of the fused formation (nx <= 16: one warp per knot).  A CTA
+// takes `kpb` consecutive knots plus one extra warp for the successor of its
+// last knot; after a CTA barrier, warp w forms Po[k] from its own Pd[k] and
+// the phi_k (= -As) and Pd[k+1] that warp w + 1 left in shared memory.  Only
+// the extra warp repeats work (one knot in kpb), and each warp's dependent
+// chain is one formation, one inversion and the two products -- the chain of
+// the three separate kernels.  The host picks kpb
+// so that the grid covers the SMs (small problems are latency-bound) and
+// raises it to FUSED_KPB_MAX for large batches (less repeated work).
+constexpr int FUSED_KPB_MAX = 16;
+
+template <typename T>
+__host__ __device__ inline size_t fused_warp_words(int nx, int nu) {
+    return (size_t)4 * nx * nx + (size_t)2 * nx * nu + 4 * nx + 2 * nu;
+}
+
+template <typename T, int NXC, int NUC>
+__global__ void __launch_bounds__(32 * (FUSED_KPB_MAX + 1))
+form_fused_warp_kernel(const SchurArgs<T> a, T *Pd, T *Po, int kpb) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = NXC ? NXC : a.nx, nu = NUC ? NUC : a.nu, n2 = nx * nx;
+    const int w = threadIdx.x / 32, t = threadIdx.x % 32;
+    const size_t words = fused_warp_words<T>(nx, nu);
+    T *Am = reinterpret_cast<T *>(smem_raw) + words * w;
+    T *As = Am + n2, *D = As + n2, *P = D + n2, *Bm = P + n2, *Bs = Bm + nx * nu,
+      *iq0 = Bs + nx * nu, *iq1 = iq0 + nx, *qs = iq1 + nx, *q1 = qs + nx, *ir = q1 + nx,
+      *rs = ir + nu;
+    T *T1 = D;  // D is dead once P = D^-1 is formed
+    const int kg = blockIdx.x * kpb + w;
+    const bool extra = w == kpb;  // formed and inverted, never written
+    int b = 0, k = 0, Nb = 0;
+    bool active = kg < a.bv.total();    // warp-uniform
+    if (active) {
+        int k0;
+        b = a.bv.owner(kg);
+        a.bv.range(b, k0, Nb);
+        k = kg - k0;
+        if (extra && k == 0) active = false;  // starts an instance: no predecessor needs it
+    }
+    bool bad = false;
+    if (active) {
+        if (k == 0) {
+            for (int i = t; i < nx; i += 32) {
+                T v = a.Qd[(size_t)kg * nx + i];
+                bad |= !good_weight(v);
+                iq1[i] = T(1) / v;
+                q1[i] = a.q[(size_t)kg * nx + i];
+            }
+            __syncwarp();
+            for (int e = t; e < n2; e += 32) {
+                int i = e / nx, j = e % nx;
+                D[e] = i == j ? iq1[i] : T(0);
+            }
+            for (int i = t; i < nx; i += 32)
+                a.gamma[(size_t)kg * nx + i] = a.c[(size_t)kg * nx + i] - q1[i] * iq1[i];
+            __syncwarp();
+        } else {
+            const int j = kg - b - 1;
+            row_blocks<T, NXC, NUC>(a, t, kg, j, Am, As, Bm, Bs, iq0, iq1, qs, ir, rs, q1, D, bad);
+            if (!extra) {
+                T *So = a.So + (size_t)j * n2;
+                for (int e = t; e < n2; e += 32) So[e] = -As[e];
+                for (int i = t; i < nx; i += 32) {
+                    T z = q1[i] * iq1[i];
+                    for (int m = 0; m < nx; ++m) z -= Am[i * nx + m] * qs[m];
+                    for (int m = 0; m < nu; ++m) z -= Bm[i * nu + m] * rs[m];
+                    a.gamma[(size_t)kg * nx + i] = a.c[(size_t)kg * nx + i] - z;
+                }
+            }
+            __syncwarp();
+        }
+        if (!extra) {
+            T *Sd = a.Sd + (size_t)kg * n2;
+            for (int e = t; e < n2; e += 32) Sd[e] = D[e];
+        }
+        __syncwarp();
+        gj_inverse_sym<T, NXC>(D, P, nx, t);
+        if (!extra)
+            for (int e = t; e < n2; e += 32) Pd[(size_t)kg * n2 + e] = P[e];
+    }
+    __syncthreads();
+    if (!active || extra) return;
+    if (k + 1 < Nb) {
+        // knot kg + 1 is warp w + 1's (the extra warp's for the last knot)
+        const T *Asn = As + words, *Pn = P + words;
+        const int j = kg - b;
+        for (int e = t; e < n2; e += 32) {
+            int i = e / nx, c = e % nx;
+            T s = T(0);
+            for (int m = 0; m < nx; ++m) s += (-Asn[i * nx + m]) * P[m * nx + c];
+            T1[e] = s;
+        }
+        __syncwarp();
+        for (int e = t; e < n2; e += 32) {
+            int i = e / nx, c = e % nx;
+            T s = T(0);
+            for (int m = 0; m < nx; ++m) s += Pn[i * nx + m] * T1[m * nx + c];
+            Po[(size_t)j * n2 + e] = -s;
+        }
+    }
+    if (a.info && __any_sync(0xffffffffu, bad) && t == 0) atomicOr(&a.info[b], MPCG_INFO_BADINPUT);
+}
+
+// ---------------------------------------------------------------------------
 // General SPD cost blocks (the Q_k, R_k of Sec. II-A's QP as full matrices).
 // A group inverts its blocks in shared memory by Gauss-Jordan elimination
 // without pivoting (positive pivots are exactly the SPD condition), then
@@ -639,6 +835,31 @@ cudaError_t launch_form_schur(const SchurArgs<T> &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Knots per CTA of the warp form for Kgrid knots on `sms` SMs.
+static inline int fused_kpb(int Kgrid, int sms) {
+    const int k = ceil_div(Kgrid, sms > 0 ? sms : 1);
+    return k < 2 ? 2 : (k > FUSED_KPB_MAX ? FUSED_KPB_MAX : k);
+}
+
+template <typename T>
+size_t form_fused_smem_bytes(int nx, int nu, int Kgrid, int sms) {
+    return fused_warp_words<T>(nx, nu) * sizeof(T) * (fused_kpb(Kgrid, sms) + 1);
+}
+
+// nx <= 16 only (one warp per knot); larger states take the separate launches.
+template <typename T>
+cudaError_t launch_form_fused(const SchurArgs<T> &a, T *Pd, T *Po, int sms, cudaStream_t s) {
+    if (group_size(a.nx) != 32) return cudaErrorInvalidValue;
+    const size_t smem = form_fused_smem_bytes<T>(a.nx, a.nu, a.Kgrid, sms);
+    const int kpb = fused_kpb(a.Kgrid, sms);
+    const dim3 grid(ceil_div(a.Kgrid, kpb)), block(32 * (kpb + 1));
+    if (a.nx == 14 && a.nu == 7)  // the Kuka arm's shape, specialised
+        form_fused_warp_kernel<T, 14, 7><<<grid, block, smem, s>>>(a, Pd, Po, kpb);
+    else
+        form_fused_warp_kernel<T, 0, 0><<<grid, block, smem, s>>>(a, Pd, Po, kpb);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_form_precon(int nx, BatchView bv, int Kgrid, const T *Sd, const T *So, T *Pd,
                                T *Po, cudaStream_t s) {
@@ -723,6 +944,8 @@ static cudaError_t form_prepare_t(int smem_optin) {
     if ((e = cudaFuncSetAttribute(recover_kernel<T>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(resid_kernel<T>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(form_schur_dense_kernel<T>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(form_fused_warp_kernel<T, 14, 7>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(form_fused_warp_kernel<T, 0, 0>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(recover_dense_kernel<T>, a, smem_optin))) return e;
     return cudaFuncSetAttribute(cgh_kernel<T>, a, smem_optin);
 }
@@ -749,6 +972,8 @@ cudaError_t form_prepare(int smem_optin) {
                                          const T *, const T *, const T *, const T *, const T *,   \
                                          const T *, T *, cudaStream_t);                           \
     template cudaError_t launch_axpy<T>(int, BatchView, int, const T *, T *, cudaStream_t);     \
+    template cudaError_t launch_form_fused<T>(const SchurArgs<T> &, T *, T *, int, cudaStream_t); \
+    template size_t form_fused_smem_bytes<T>(int, int, int, int);                                \
     template cudaError_t launch_recover_dense<T>(int, int, BatchView, int, const T *, const T *, \
                                                  const T *, const T *, const T *, const T *,     \
                                                  const T *, T *, T *, cudaStream_t);

@@ -17,7 +17,7 @@ namespace mpcg {
 namespace {
 
 constexpr int LIN_THREADS = 128;  // 4 knots per block, one warp each
-constexpr int MERIT_THREADS = 64;   // one knot per thread; a block per chunk of 64 knots
+constexpr int MERIT_THREADS = 64;   // one (knot, joint) pair per thread
 constexpr int MAX_ALPHA = 32;
 
 template <typename T>
@@ -126,10 +126,14 @@ linearize_kernel(ModelView<T> m, BatchView bv, const T *__restrict__ X, const T 
 // J + mu_b (||x'_0 - x_s||_1 + sum ||x'_{k+1} - f(x'_k, u'_k)||_1).  The
 // candidate point is rounded to the working type first, as the applied step
 // will be.  mu_b = mu when mu > 0, else 1.1 max(1, max |lambda_b|).  Block
-// (b, a, chunk) takes 64 knots of instance b, one per thread, and adds its
-// share to merit[b][a] (zeroed before the launch) with an FP64 atomic: the
-// FP64 work spreads over many SMs, and the summation order only moves the
-// merits by rounding, far below the tie tolerance of the choice.
+// (b, a, chunk) takes 64 (knot, joint) pairs of instance b, one per thread:
+// thread (k, i) adds the cost of state rows i and h + i of knot k (and of
+// input i, nu <= h), and the defects of those two rows, which need joint i's
+// velocity update alone.  Its share goes to merit[b][a] (zeroed before the
+// launch) with an FP64 atomic: the FP64 work (one sine per pair) spreads
+// over h times more threads than one knot per thread would, and the
+// summation order only moves the merits by rounding, far below the tie
+// tolerance of the choice.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -166,10 +170,10 @@ merit_kernel(ModelView<T> m, BatchView bv, int n_alpha, const T *__restrict__ X,
     if (b >= bv.B) return;
     int k0, Nb;
     bv.range(b, k0, Nb);
-    const int kbase = blockIdx.y * MERIT_THREADS;
-    if (kbase >= Nb) return;  // whole block: this instance is shorter
+    const int nx = m.nx, nu = m.nu, h = m.h;
+    const int ebase = blockIdx.y * MERIT_THREADS;
+    if (ebase >= Nb * h) return;  // whole block: this instance is shorter
     const int c0 = k0 - b;
-    const int nx = m.nx, nu = m.nu;
     const T alpha = T(ldexp(1.0, -a));
     double mub = mu;
     if (!(mu > 0.0)) {
@@ -187,34 +191,41 @@ merit_kernel(ModelView<T> m, BatchView bv, int n_alpha, const T *__restrict__ X,
         mub = 1.1 * fmax(1.0, block_max<T>((double)mx, red));
     }
     double J = 0.0, viol = 0.0;
-    const int k = kbase + threadIdx.x;
-    if (k < Nb) {
-        T xp[64], up[32], xk[64];  // candidate x'_{k-1}, u'_{k-1}, x'_k (nx <= 64, nu <= 32)
+    const int e = ebase + threadIdx.x;
+    if (e < Nb * h) {
+        const int k = e / h, i = e % h;
         const size_t o = (size_t)(k0 + k) * nx;
         const bool last = k + 1 >= Nb;
-        for (int i = 0; i < nx; ++i) {
-            xk[i] = X[o + i] + alpha * dX[o + i];
-            const double e = (double)xk[i] - (double)xref[o + i];
-            J += 0.5 * (double)(last ? m.wf[i] : m.wq[i]) * e * e;
+        // candidate position and velocity of joint i at knot k
+        const T pk = X[o + i] + alpha * dX[o + i];
+        const T vk = X[o + h + i] + alpha * dX[o + h + i];
+        const T *w = last ? m.wf : m.wq;
+        const double ep = (double)pk - (double)xref[o + i];
+        const double ev = (double)vk - (double)xref[o + h + i];
+        J += 0.5 * (double)w[i] * ep * ep;
+        J += 0.5 * (double)w[h + i] * ev * ev;
+        if (!last && i < nu) {
+            const size_t ou = (size_t)(c0 + k) * nu + i;
+            const T ui = U[ou] + alpha * dU[ou];
+            J += 0.5 * (double)m.wr[i] * (double)ui * (double)ui;
         }
-        if (!last)
-            for (int i = 0; i < nu; ++i) {
-                const T ui = U[(size_t)(c0 + k) * nu + i] + alpha * dU[(size_t)(c0 + k) * nu + i];
-                J += 0.5 * (double)m.wr[i] * (double)ui * (double)ui;
-            }
         if (k == 0) {
-            for (int i = 0; i < nx; ++i) viol += fabs((double)xk[i] - (double)xs[(size_t)b * nx + i]);
+            viol += fabs((double)pk - (double)xs[(size_t)b * nx + i]);
+            viol += fabs((double)vk - (double)xs[(size_t)b * nx + h + i]);
         } else {
-            const size_t op = o - nx;
-            for (int i = 0; i < nx; ++i) xp[i] = X[op + i] + alpha * dX[op + i];
-            for (int i = 0; i < nu; ++i)
-                up[i] = U[(size_t)(c0 + k - 1) * nu + i] + alpha * dU[(size_t)(c0 + k - 1) * nu + i];
-            // each joint's velocity update once, then both of its rows
-            for (int i = 0; i < m.h; ++i) {
-                const double vn = vnext<T, double>(m, i, xp, up);
-                viol += fabs((double)xk[i] - ((double)xp[i] + m.dt * vn));
-                viol += fabs((double)xk[m.h + i] - vn);
+            // joint i's velocity update from the candidate (x'_{k-1}, u'_{k-1})
+            const size_t op = o - nx, ou = (size_t)(c0 + k - 1) * nu;
+            const T pp = X[op + i] + alpha * dX[op + i];
+            const T vp = X[op + h + i] + alpha * dX[op + h + i];
+            double f = 0.0;
+            for (int j = 0; j < nu; ++j) {
+                const T uj = U[ou + j] + alpha * dU[ou + j];
+                f += (double)m.P[i * nu + j] * (double)uj;
             }
+            f += -(double)m.damp[i] * (double)vp - (double)m.stiff[i] * sin((double)pp);
+            const double vn = (double)vp + m.dt * f;
+            viol += fabs((double)pk - ((double)pp + m.dt * vn));
+            viol += fabs((double)vk - vn);
         }
     }
     const double part = block_sum<T>(J + mub * viol, red);
@@ -315,7 +326,7 @@ int line_search_t(const mpcg_dims &d, int B, const int *knot_off, const mpcg_mod
     const BatchView bv = bview(knot_off, B, d.N);
     int rc = err(cudaMemsetAsync(merit, 0, sizeof(double) * (size_t)B * n_alpha, st));
     if (rc) return rc;
-    const dim3 grid(B * n_alpha, (d.N + MERIT_THREADS - 1) / MERIT_THREADS);
+    const dim3 grid(B * n_alpha, (d.N * (d.nx / 2) + MERIT_THREADS - 1) / MERIT_THREADS);
     merit_kernel<T><<<grid, MERIT_THREADS, 0, st>>>(
         view<T>(m), bv, n_alpha, (const T *)X, (const T *)U, (const T *)dX, (const T *)dU,
         (const T *)xref, (const T *)xs, (const T *)lam, mu, merit);

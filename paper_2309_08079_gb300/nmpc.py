@@ -1,9 +1,9 @@
 """SQP outer loop on the device around the solve path (Sec. II-A Steps 1-3,
 Sec. IV-C), on the library's synthetic model (mpcg_model in include/mpcg.h).
 
-One SQP iteration is six stream-ordered library calls with no host
-synchronisation: linearise at the current trajectory, form S+ and gamma, form
-the stair preconditioner, PCG (warm-started from the previous iteration's
+One SQP iteration is five stream-ordered library calls with no host
+synchronisation: linearise at the current trajectory, form S+, gamma and the
+stair preconditioner (one fused launch), PCG (warm-started from the previous iteration's
 multipliers, as the paper does), recover the step, and the parallel line
 search that evaluates every step size of a halving set and applies the one
 with the smallest L1 merit.  `SQP.graph()` captures iterations in a CUDA
@@ -110,8 +110,7 @@ class SQP:
         """One SQP iteration (no host synchronisation)."""
         s, lq = self.s, self.lq
         self.linearize(stream)
-        s.form_schur(lq, self.schur, stream)
-        s.form_precon(lq, self.schur, stream)
+        s.form(lq, self.schur, stream)
         s.pcg_solve(lq, self.schur, self.lam, self.opts, self.stats, self.ws, stream)
         s.recover_step(lq, self.lam, self.dx, self.du, stream)
         self.line_search(stream)

@@ -195,6 +195,18 @@ class Solver:
         L.check("mpcg_form_precon", rc)
         return schur
 
+    def form(self, lq: LQTensors, schur: SchurTensors, stream=None) -> SchurTensors:
+        """form_schur and form_precon in one launch (mpcg_form_schur_precon)."""
+        ls, ss = lq.lq_struct(), schur.struct()
+        if lq.batched:
+            rc = self.lib.mpcg_form_schur_precon_batched(self.h, lq.dims(), lq.nb, _ptr(lq.knot_off),
+                                                         C.byref(ls), C.byref(ss), _stream(stream))
+        else:
+            rc = self.lib.mpcg_form_schur_precon(self.h, lq.dims(), C.byref(ls), C.byref(ss),
+                                                 _stream(stream))
+        L.check("mpcg_form_schur_precon", rc)
+        return schur
+
     def pcg_solve(self, lq: LQTensors, schur: SchurTensors, lam: torch.Tensor, opts=None,
                   stats: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
                   stream=None, N: Optional[int] = None) -> torch.Tensor:
@@ -260,8 +272,8 @@ class Solver:
     def solve(self, lq: LQTensors, lam0: Optional[torch.Tensor] = None, opts=None,
               schur: Optional[SchurTensors] = None, stats=None, workspace=None, stream=None,
               refine: int = 0):
-        """The whole path: form_schur, form_precon, pcg_solve, `refine` steps of
-        iterative refinement, recover_step.
+        """The whole path: form_schur and form_precon (one fused launch),
+        pcg_solve, `refine` steps of iterative refinement, recover_step.
 
         Returns (lam, dx, du, stats, schur); lam0 (if given) is overwritten.
         stats are those of the first PCG solve.
@@ -270,8 +282,7 @@ class Solver:
             schur = self.alloc_schur(lq)
         lam = lam0 if lam0 is not None else torch.zeros(lq.total, lq.nx, dtype=lq.dtype,
                                                         device=lq.device)
-        self.form_schur(lq, schur, stream)
-        self.form_precon(lq, schur, stream)
+        self.form(lq, schur, stream)
         stats = self.pcg_solve(lq, schur, lam, opts, stats, workspace, stream)
         if refine > 0:
             if workspace is None:

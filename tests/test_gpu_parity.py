@@ -279,3 +279,63 @@ def test_wide_cluster_parity(nx, nu, N, dtype):
     assert st["status"][0] == 0, st
     bar = TOL_F32 if f32 else TOL_F64
     assert e_lam < bar and e_dz < bar, (e_lam, e_dz)
+
+
+# ------------------------------------------------------------------ fused formation
+def _ragged(B, seed):
+    return [int(n) for n in gen.batch_horizons(B, 1, 512, seed)]
+
+
+@pytest.mark.parametrize("nx,nu,Ns,dtype", [(14, 7, [1], "float32"), (14, 7, [2], "float32"),
+                                            (14, 7, [17], "float32"), (14, 7, [512], "float32"),
+                                            (36, 12, [40], "float32"), (14, 7, [100], "float64"),
+                                            (14, 7, [40, 1, 129, 2], "float32"), (6, 3, [9, 30], "float64"),
+                                            (14, 7, _ragged(80, 1), "float32"),
+                                            (16, 8, _ragged(80, 2), "float64")])
+def test_fused_formation_equals_the_two_calls(nx, nu, Ns, dtype):
+    """mpcg_form_schur_precon writes what form_schur then form_precon write:
+    the same formulas in the same order, so the two agree to rounding (the
+    fused kernel's compile-time loop shapes let the compiler contract other
+    multiply-adds: ~1 ulp per entry), the flags exactly.  The ragged batches
+    of 80 instances run the launch with the most knots per CTA, and instance
+    boundaries fall on every position within a CTA."""
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors
+    tdt = torch.float32 if dtype == "float32" else torch.float64
+    npdt = np.float32 if dtype == "float32" else np.float64
+    s = solver()
+    if len(Ns) == 1:
+        lt = LQTensors.from_numpy(gen.kuka_lq(nx, nu, Ns[0], 990 + Ns[0]).astype(npdt), dtype=tdt)
+    else:
+        lt = LQTensors.from_batch(gen.kuka_batch(nx, nu, Ns, 990).astype(npdt), dtype=tdt)
+    a, b = s.alloc_schur(lt), s.alloc_schur(lt)
+    s.form_schur(lt, a)
+    s.form_precon(lt, a)
+    s.form(lt, b)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(a.info.cpu().numpy(), b.info.cpu().numpy())
+    eps = np.finfo(npdt).eps
+    K, C = lt.total, lt.total - lt.nb
+    for f, n, tol in (("Sd", K, 8 * eps), ("So", C, 0.0), ("gamma", K, 8 * eps),
+                      ("Pd", K, 64 * eps), ("Po", C, 64 * eps)):
+        if n == 0:
+            continue
+        x = getattr(a, f)[:n].cpu().double().numpy()
+        y = getattr(b, f)[:n].cpu().double().numpy()
+        # per block (per knot), normwise: the blocks' scales differ by orders
+        ax = tuple(range(1, x.ndim))
+        err = np.sqrt(((x - y) ** 2).sum(axis=ax)) / np.maximum(np.sqrt((x ** 2).sum(axis=ax)), 1e-300)
+        assert err.max() <= tol, (f, float(err.max()), float(tol))
+
+
+def test_fused_formation_flags_bad_input():
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors
+    lq = gen.kuka_lq(14, 7, 20, 3)
+    lq.Rd[4, 1] = 0.0
+    s = solver()
+    lt = LQTensors.from_numpy(lq.astype(np.float32))
+    sch = s.alloc_schur(lt)
+    s.form(lt, sch)
+    torch.cuda.synchronize()
+    assert int(sch.info.cpu()[0]) == 1
