@@ -121,8 +121,15 @@ typedef struct {
     const int *instances;
     int n_instances;
     /* Preconditioner applied by the PCG: 0 the symmetric stair Phi^-1 of
-       Sec. IV-A (Pd and Po, the default); 1 block Jacobi, Phi^-1 = D^-1 (Pd
-       only; Po is not read), for comparison.  Other values: MPCG_EINVAL. */
+       Sec. IV-A (Pd and Po, the default); for comparison, 1 block Jacobi,
+       Phi^-1 = D^-1 (Pd only; Po is not read), and 2 the non-symmetric
+       stair preconditioner of the work Sec. IV-A cites: the inverse of the
+       stair matrix whose odd block rows (instance-local knot k odd) keep
+       their off-diagonal blocks of S+, i.e. the rows of Phi^-1 at odd k and
+       only Pd[k] at even k (same Pd, Po arrays).  It is not symmetric, so
+       PCG has no convergence guarantee with it (on the Kuka-shaped workload
+       it stalls from N = 32 on; it exists to show why the paper symmetrises
+       it).  Other values: MPCG_EINVAL. */
     int precon;
 } mpcg_opts;
 

@@ -7,7 +7,8 @@ take their inputs from ``workload``.
 """
 from .oracle import (  # noqa: F401
     build, kkt_solve, kkt_solve_rhs, kkt_dim, schur_blocks, precon_blocks, jacobi_blocks,
-    dense_S, dense_Phi_inv, block_tridiag_sparse, pcg, recover, grad, loss,
+    dense_S, dense_Phi_inv, block_tridiag_sparse, stair_matrix, stair_inverse, pcg, pcg_op,
+    recover, grad, loss,
     solve_batch, natural_z, split_z, relerr,
 )
 from . import nmpc  # noqa: F401

@@ -12,7 +12,12 @@ Functions and the passage each follows:
                  definition, Sec. II-B (Eq. schur), as sparse products.
   precon_blocks  symmetric stair preconditioner Phi^-1, Sec. IV-A: diagonal
                  blocks D_k^-1, off-diagonal blocks -D_{k+1}^-1 phi_k D_k^-1.
-  pcg            Algorithm 1 (PCG) with the exit tests described below.
+  stair_matrix,  the non-symmetric stair matrix of S+ (odd block rows keep
+  stair_inverse  their neighbours) and its closed-form inverse: the
+                 comparison preconditioner of the work Sec. IV-A cites.
+  jacobi_blocks  block Jacobi Phi^-1 = D^-1 (comparison preconditioner).
+  pcg, pcg_op    Algorithm 1 (PCG) with the exit tests described below
+                 (pcg_op: operators as matrices, Phi^-1 may be non-symmetric).
   recover        dz = -G^-1 (g - C^T lambda), Sec. II-B (Eq. schur).
   grad           gradient of a scalar loss of (lambda, dz) through the exact
                  KKT solution (implicit-function theorem on Eq. KKT).
@@ -236,6 +241,43 @@ def jacobi_blocks(Sd: np.ndarray, So: np.ndarray):
     return np.linalg.inv(Sd), np.zeros_like(So)
 
 
+def stair_matrix(Sd: np.ndarray, So: np.ndarray, odd: bool = True) -> sp.csr_matrix:
+    """The (non-symmetric) stair matrix of S+: every block row keeps its
+    diagonal block; the odd block rows (even ones if odd=False) also keep
+    their two off-diagonal blocks of S+.  The preconditioner the symmetric
+    stair preconditioner of Sec. IV-A (and its cited work) is built from."""
+    N = Sd.shape[0]
+    blocks = [[None] * N for _ in range(N)]
+    for k in range(N):
+        blocks[k][k] = sp.csr_matrix(Sd[k])
+        if (k % 2 == 1) == odd:
+            if k >= 1:
+                blocks[k][k - 1] = sp.csr_matrix(So[k - 1])
+            if k + 1 < N:
+                blocks[k][k + 1] = sp.csr_matrix(So[k].T)
+    return sp.bmat(blocks, format="csr")
+
+
+def stair_inverse(Sd: np.ndarray, So: np.ndarray, odd: bool = True) -> sp.csr_matrix:
+    """Inverse of stair_matrix(Sd, So, odd), in closed form: block row k is
+    D_k^-1 alone in the rows without neighbours; in the others it is
+    (-D_k^-1 O_{k,k-1} D_{k-1}^-1, D_k^-1, -D_k^-1 O_{k,k+1} D_{k+1}^-1),
+    because the neighbouring rows of such a row are diagonal.  These are the
+    rows of the symmetric stair Phi^-1 with the other rows' off-diagonal
+    blocks dropped."""
+    N = Sd.shape[0]
+    Pd = np.linalg.inv(Sd)
+    blocks = [[None] * N for _ in range(N)]
+    for k in range(N):
+        blocks[k][k] = sp.csr_matrix(Pd[k])
+        if (k % 2 == 1) == odd:
+            if k >= 1:
+                blocks[k][k - 1] = sp.csr_matrix(-Pd[k] @ So[k - 1] @ Pd[k - 1])
+            if k + 1 < N:
+                blocks[k][k + 1] = sp.csr_matrix(-Pd[k] @ So[k].T @ Pd[k + 1])
+    return sp.bmat(blocks, format="csr")
+
+
 def block_tridiag_sparse(Dd: np.ndarray, Do: np.ndarray) -> sp.csr_matrix:
     """Assemble a symmetric block-tridiagonal matrix from Dd and Do (below)."""
     N, nx, _ = Dd.shape
@@ -278,8 +320,14 @@ def pcg(Sd, So, Pd, Po, b, lam0=None, tol=1e-6, tol_mode=0, max_iter=None):
     A starting point that already passes the test returns with 0 iterations.
     Returns (lambda, iterations, converged).
     """
-    S = block_tridiag_sparse(Sd, So)
-    P = block_tridiag_sparse(Pd, Po)
+    return pcg_op(block_tridiag_sparse(Sd, So), block_tridiag_sparse(Pd, Po), b, lam0, tol,
+                  tol_mode, max_iter)
+
+
+def pcg_op(S, P, b, lam0=None, tol=1e-6, tol_mode=0, max_iter=None):
+    """Algorithm 1 with S+ and Phi^-1 given as (sparse) matrices; Phi^-1 may
+    be non-symmetric (the stair preconditioner).  Same exits and returns as
+    pcg()."""
     b = _f64(b).ravel()
     n = b.size
     lam = np.zeros(n) if lam0 is None else _f64(lam0).ravel().copy()

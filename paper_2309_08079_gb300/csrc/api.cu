@@ -265,7 +265,7 @@ int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const 
     P.tol_mode = o ? o->tol_mode : 0;
     P.max_iter = o ? o->max_iter : 0;
     P.precon = o ? o->precon : 0;
-    if (P.precon != 0 && P.precon != 1) return MPCG_EINVAL;
+    if (P.precon < 0 || P.precon > 2) return MPCG_EINVAL;
     P.inst_list = (o && o->instances && o->n_instances > 0) ? o->instances : nullptr;
     P.n_tickets = P.inst_list ? o->n_instances : B;
     if (P.inst_list && !knot_off) return MPCG_EINVAL;

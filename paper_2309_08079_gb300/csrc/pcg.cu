@@ -268,7 +268,9 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
         const T *pPd = nullptr, *pPl = nullptr, *pPu = nullptr;
         const int nx2 = nx * nx;
 
-        const bool jac = P.precon == 1;
+        // Phi^-1 rows without off-diagonal blocks: every row for block Jacobi
+        // (precon 1), the even knots' rows for the stair preconditioner (2)
+        const bool jac = P.precon == 1 || (P.precon == 2 && (k & 1) == 0);
         if (!bad) {
             if constexpr (MODE == MODE_REG) {
                 const bool hl = active_knot && k >= 1, hu = active_knot && k + 1 < Nb;
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
                     if (k >= 1) { pSl = P.So + (size_t)(c0 + k - 1) * nx2; pPl = P.Po + (size_t)(c0 + k - 1) * nx2; }
                     if (k + 1 < Nb) { pSu = P.So + (size_t)(c0 + k) * nx2; pPu = P.Po + (size_t)(c0 + k) * nx2; }
                 }
-                if (jac) pPl = pPu = nullptr;  // block Jacobi: Phi^-1 = D^-1
+                if (jac) pPl = pPu = nullptr;
             }
         }
 

@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(512, 1) pcg_cta_kernel(const PcgParams<T> P) {
         auto blocks = [&](int k, bool precon, const T *&D, const T *&Lo, const T *&U) {
             const T *Md = precon ? P.Pd : P.Sd;
             const T *Mo = precon ? P.Po : P.So;
-            const bool off = !(precon && P.precon == 1);  // block Jacobi: Phi^-1 = D^-1
+            // Phi^-1 rows without off-diagonal blocks: all (block Jacobi,
+            // precon 1) or the even knots' (stair, precon 2)
+            const bool off = !(precon && (P.precon == 1 || (P.precon == 2 && (k & 1) == 0)));
             D = Md + (size_t)(k0 + k) * nx2;
             Lo = (off && k >= 1) ? Mo + (size_t)(c0 + k - 1) * nx2 : nullptr;
             U = (off && k + 1 < Nb) ? Mo + (size_t)(c0 + k) * nx2 : nullptr;
@@ -534,7 +536,8 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
             const T *Md = (i_ps & 1) ? P.Pd : P.Sd;
             const T *Mo = (i_ps & 1) ? P.Po : P.So;
             const uint32_t bar = mbs + (uint32_t)(i_m * sizeof(uint64_t));
-            // block Jacobi passes (odd, Phi^-1) use no off-diagonal blocks
+            // block Jacobi passes (odd, Phi^-1) use no off-diagonal blocks; a
+            // stair pass needs O_k in row k (k odd) or in row k + 1 (k even)
             const bool hasU = k + 1 < Nb && !((i_ps & 1) && P.precon == 1);
             mbar_arrive_expect(bar, hasU ? 2u * nxb : nxb);
             bulk_g2s(smem_u32(tile(i_d)), Md + (size_t)(k0 + k) * nx2, nxb, bar);
@@ -586,7 +589,7 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
                 }
                 if (act) {
                     const int k = ks0 + t;
-                    const bool off = !((ps & 1) && P.precon == 1);
+                    const bool off = !((ps & 1) && (P.precon == 1 || (P.precon == 2 && (k & 1) == 0)));
                     const T *D = tile(c_d);
                     const T *U = (off && k + 1 < Nb) ? tile(RD + c_o) : nullptr;
                     const T *Lt = (off && k >= 1 && t >= 1) ? tile(RD + c_op) : nullptr;

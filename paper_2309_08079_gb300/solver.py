@@ -121,7 +121,8 @@ def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0, mode=0, instances=Non
     when blocks are not 16-byte multiples), 4 cluster per instance with
     shared-memory operators and up to 64 knots per CTA (nx <= 16).  precon:
     0 symmetric stair
-    (Sec. IV-A), 1 block Jacobi."""
+    (Sec. IV-A), 1 block Jacobi, 2 the non-symmetric stair preconditioner
+    (comparison only: no convergence guarantee)."""
     o = L.mpcg_opts(float(tol), int(tol_mode), int(max_iter), int(cluster), int(mode), None, 0,
                     int(precon))
     if instances is not None:  # a device int32 tensor of instance indices

@@ -240,8 +240,70 @@ def test_block_jacobi_parity(nx, nu, N, dtype, mode):
 def test_precon_value_is_checked():
     from paper_2309_08079_gb300.solver import make_opts
     from paper_2309_08079_gb300._lib import MPCGError
-    with pytest.raises(MPCGError):
-        run_gpu(gen.kuka_lq(14, 7, 16, 1).astype(np.float32), opts=make_opts(precon=2))
+    for bad in (-1, 3):
+        with pytest.raises(MPCGError):
+            run_gpu(gen.kuka_lq(14, 7, 16, 1).astype(np.float32), opts=make_opts(precon=bad))
+
+
+# ------------------------------------------------------------------ stair (non-symmetric) comparison preconditioner
+def _stair_oracle_iterate(lq_in, m):
+    Sd, So, g = oracle.schur_blocks(lq_in.astype(np.float64))
+    S = oracle.block_tridiag_sparse(Sd, So)
+    lam, it, _ = oracle.pcg_op(S, oracle.stair_inverse(Sd, So), -g, tol=1e-30, max_iter=m)
+    assert it == m
+    return lam
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("nx,nu,dtype", [(14, 7, "float32"), (14, 7, "float64"), (36, 12, "float32"),
+                                         (4, 2, "float32")])
+def test_stair_precon_iterates_match_the_oracle(nx, nu, dtype, mode):
+    """opts.precon = 2 in every kernel form: after a fixed number of PCG
+    iterations lambda equals the oracle's Algorithm 1 iterate with the stair
+    inverse (odd knots' rows of Phi^-1, Pd alone at even knots) for the same
+    count; the two stair variants' iterates differ by ~10 % and the
+    symmetric one's by ~100 %, so a misplaced row mask fails.  The solve
+    reports NOT_CONVERGED at max_iter."""
+    from paper_2309_08079_gb300.solver import make_opts
+    f32 = dtype == "float32"
+    m = 12
+    lq_in = gen.kuka_lq(nx, nu, 40, 880 + nx).astype(np.float32 if f32 else np.float64)
+    lam, _, _, st, _ = run_gpu(lq_in, dtype, opts=make_opts(mode=mode, precon=2, tol=1e-30, max_iter=m))
+    assert st["status"][0] == 1 and st["iters"][0] == m, st
+    e = oracle.relerr(lam, _stair_oracle_iterate(lq_in, m))
+    assert e < (1e-3 if f32 else 1e-9), e
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_stair_precon_parity_in_a_ragged_batch(mode):
+    """The row mask follows each instance's own knot index in a batch
+    (instances of odd and even lengths back to back)."""
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    m, Ns = 10, [17, 40, 1, 33, 8]
+    batch = gen.kuka_batch(14, 7, Ns, 890).astype(np.float32)
+    s = solver()
+    lt = LQTensors.from_batch(batch)
+    lam, _, _, st, _ = s.solve(lt, None, opts=make_opts(mode=mode, precon=2, tol=1e-30, max_iter=m))
+    torch.cuda.synchronize()
+    st = read_stats(st)
+    lam = lam.cpu().double().numpy()
+    for i, N in enumerate(Ns):
+        lo = _stair_oracle_iterate(gen.kuka_lq(14, 7, N, 890 + i).astype(np.float32), m) if N > 1 else None
+        k0 = int(batch.knot_off[i])
+        if N == 1:  # one knot: Phi^-1 = S+^-1 exactly, converged after one iteration
+            assert st["status"][i] == 0
+            continue
+        assert st["status"][i] == 1 and st["iters"][i] == m, (i, st)
+        assert oracle.relerr(lam[k0:k0 + N], lo) < 1e-3, i
+
+
+def test_stair_precon_converges_on_a_short_horizon():
+    """N = 8, where Algorithm 1 with the stair preconditioner still
+    converges: the KKT solution."""
+    from paper_2309_08079_gb300.solver import make_opts
+    e_lam, e_dz, st = parity(gen.kuka_lq(14, 7, 8, 10), opts=make_opts(precon=2))
+    assert st["status"][0] == 0 and e_lam < TOL_F32 and e_dz < TOL_F32, (e_lam, e_dz, st)
 
 
 @pytest.mark.parametrize("mode", [1, 2, 3])

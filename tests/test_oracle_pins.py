@@ -337,6 +337,58 @@ def test_symmetric_stair_needs_fewer_iterations_than_block_jacobi():
 
 
 
+# ---------------------------------------------------------------- stair (non-symmetric) comparison preconditioner
+@pytest.mark.parametrize("N", [1, 2, 7, 12])
+@pytest.mark.parametrize("odd", [True, False])
+def test_stair_inverse_inverts_the_stair_matrix(N, odd):
+    """The closed-form stair inverse against the stair matrix built from the
+    blocks of S+ directly (dense product = identity), and its pattern: rows
+    without neighbours hold D_k^-1 alone."""
+    lq = gen.kuka_lq(6, 3, N, 40 + N)
+    Sd, So, _ = oracle.schur_blocks(lq)
+    P = oracle.stair_matrix(Sd, So, odd).toarray()
+    Pi = oracle.stair_inverse(Sd, So, odd).toarray()
+    assert np.abs(Pi @ P - np.eye(P.shape[0])).max() < 1e-10
+    nx = 6
+    for k in range(N):
+        if (k % 2 == 1) != odd:
+            row = Pi[k * nx:(k + 1) * nx]
+            off = np.delete(row, np.s_[k * nx:(k + 1) * nx], axis=1)
+            assert np.all(off == 0.0)
+
+
+def test_symmetric_stair_is_the_sum_of_the_two_stair_inverses():
+    """Phi^-1 of Sec. IV-A = P_odd^-1 + P_even^-1 - D^-1 with each stair
+    matrix inverted densely (np.linalg.inv, not the closed form): pins
+    precon_blocks through the construction of the cited work."""
+    lq = gen.kuka_lq(14, 7, 9, 77)
+    Sd, So, _ = oracle.schur_blocks(lq)
+    Pd, Po = oracle.precon_blocks(Sd, So)
+    Phi = oracle.block_tridiag_sparse(Pd, Po).toarray()
+    Lo = np.linalg.inv(oracle.stair_matrix(Sd, So, True).toarray())
+    Le = np.linalg.inv(oracle.stair_matrix(Sd, So, False).toarray())
+    Dinv = np.linalg.inv(oracle.block_tridiag_sparse(Sd, np.zeros_like(So)).toarray())
+    assert np.abs(Lo + Le - Dinv - Phi).max() <= 1e-10 * np.abs(Phi).max()
+
+
+def test_stair_pcg_converges_on_a_short_horizon_and_not_on_a_long_one():
+    """The reason for the symmetric form: with the non-symmetric stair
+    preconditioner Algorithm 1 loses its guarantees.  On the Kuka-shaped
+    workload it still reaches the KKT solution at N = 8 but stalls at
+    N = 32 (10 N nx iterations), where the symmetric stair converges."""
+    for N, expect in ((8, True), (32, False)):
+        lq = gen.kuka_lq(14, 7, N, 2 + N)
+        Sd, So, g = oracle.schur_blocks(lq)
+        S = oracle.block_tridiag_sparse(Sd, So)
+        lam, it, ok = oracle.pcg_op(S, oracle.stair_inverse(Sd, So), -g, tol=1e-8)
+        assert ok == expect, (N, it)
+        if ok:
+            lo, _, _ = oracle.kkt_solve(lq)
+            assert oracle.relerr(lam, lo) < 1e-6
+    _, _, ok = oracle.pcg(Sd, So, *oracle.precon_blocks(Sd, So), -g, tol=1e-8)
+    assert ok
+
+
 # ---------------------------------------------------------------- dense SPD cost blocks
 def test_dense_blocks_with_diagonal_values_match_the_diagonal_problem():
     """Q_k = diag(Qd_k), R_k = diag(Rd_k) given as dense blocks: the same
