@@ -144,7 +144,17 @@ int choose_pcg_cluster(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opt
     else if (nx <= 64) { L.lpk = 32; L.rpt = 2; }
     else return MPCG_EUNSUPPORTED;
     const int kpc_cap = max_threads / L.lpk;  // knot slots per CTA
-    int C = (o && o->cluster > 0) ? o->cluster : ceil_div(d.N, kpc_cap);
+    // A single instance runs fastest spread over more CTAs than it fills:
+    // register form (float32, nx = 14) at about 8 knots per CTA (fewer warps
+    // per CTA barrier and reduction tree; measured on GB300, N = 64 / 128:
+    // 402 / 697 us against 447 / 765 us with full 32-knot CTAs), the shared-
+    // memory form at the largest cluster (each lane's rows per iteration grow
+    // with the knots per CTA: FP64 N = 128 4.9 ms at 16 CTAs against 13.0 ms
+    // at 4; nx = 36 N = 64 2.0 against 4.3 ms).  Batches fill the CTAs (the
+    // autotuner tries the other packings).
+    const int kpc_pref = B > 1 ? kpc_cap : (reg ? std::min(kpc_cap, 8) : 1);
+    int C = (o && o->cluster > 0) ? o->cluster : std::min(kMaxCluster, ceil_div(d.N, kpc_pref));
+    if (!(o && o->cluster > 0)) C = std::max(C, ceil_div(d.N, kpc_cap));
     if (C > kMaxCluster) return MPCG_EUNSUPPORTED;
     C = std::max(1, std::min(C, d.N));
     for (;;) {
