@@ -381,6 +381,18 @@ int mpcg_line_search_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *k
                              const void *lambda, double mu, int n_alpha, double *merit,
                              int *alpha_index, void *stream);
 
+/* Diagnostic of the bounded device waits (not in the paper).  Every PCG
+ * exchange completes on an mbarrier filled by peer CTAs' st.async pushes and
+ * is awaited with a %globaltimer deadline, so a missing push ends the solve
+ * with MPCG_TIMEOUT instead of hanging.  This call runs that pattern in one
+ * two-CTA cluster: each CTA expects 4 bytes on its own mbarrier, pushes 4
+ * bytes to the other only if `push` is non-zero, and waits at most limit_s
+ * seconds (1e-6 <= limit_s <= 1, else MPCG_EINVAL).  `status` is a DEVICE
+ * int[2] that receives, per CTA, MPCG_CONVERGED if its wait completed with
+ * the pushed value and MPCG_TIMEOUT if it gave up.  With push = 0 both waits
+ * run out by construction; the context stays usable. */
+int mpcg_selftest_wait(mpcg_handle *h, int push, double limit_s, int *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -34,7 +34,7 @@ EXPORTS = (
     "mpcg_recover_step_batched", "mpcg_backward_batched", "mpcg_backward",
     "mpcg_backward_batched_noalloc", "mpcg_refine_step", "mpcg_refine_step_batched",
     "mpcg_linearize", "mpcg_linearize_batched", "mpcg_line_search", "mpcg_line_search_batched",
-    "mpcg_form_schur_precon", "mpcg_form_schur_precon_batched",
+    "mpcg_form_schur_precon", "mpcg_form_schur_precon_batched", "mpcg_selftest_wait",
 )
 
 
@@ -149,6 +149,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.mpcg_line_search_batched.restype = i32
     lib.mpcg_line_search_batched.argtypes = [vp, mpcg_dims, i32, vp, P(mpcg_model), vp, vp, vp, vp,
                                              vp, vp, vp, C.c_double, i32, vp, vp, vp]
+    lib.mpcg_selftest_wait.restype = i32
+    lib.mpcg_selftest_wait.argtypes = [vp, i32, C.c_double, vp, vp]
     _lib = lib
     return lib
 

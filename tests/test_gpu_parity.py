@@ -401,3 +401,37 @@ def test_fused_formation_flags_bad_input():
     s.form(lt, sch)
     torch.cuda.synchronize()
     assert int(sch.info.cpu()[0]) == 1
+
+
+# ------------------------------------------------------------------ bounded waits
+def test_bounded_wait_runs_out_and_reports_timeout():
+    """The exchange pattern of the PCG kernels (mbarrier filled by a peer's
+    st.async, awaited with a %globaltimer deadline) in a two-CTA cluster:
+    with the pushes withheld both waits give up after 2 ms and report
+    MPCG_TIMEOUT; with them both complete; the context stays usable and a
+    solve afterwards is still correct."""
+    import time
+    import torch
+    from paper_2309_08079_gb300._lib import MPCG_TIMEOUT, check
+    s = solver()
+    st = torch.full((2,), -1, dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    check("mpcg_selftest_wait", s.lib.mpcg_selftest_wait(s.h, 0, 2e-3, st.data_ptr(), None))
+    torch.cuda.synchronize()
+    assert st.cpu().tolist() == [MPCG_TIMEOUT, MPCG_TIMEOUT]
+    assert time.perf_counter() - t0 < 5.0
+    st.fill_(-1)
+    check("mpcg_selftest_wait", s.lib.mpcg_selftest_wait(s.h, 1, 2e-3, st.data_ptr(), None))
+    torch.cuda.synchronize()
+    assert st.cpu().tolist() == [0, 0]
+    e_lam, e_dz, stt = parity(gen.kuka_lq(14, 7, 64, 65))
+    assert stt["status"][0] == 0 and e_lam < TOL_F32 and e_dz < TOL_F32
+
+
+def test_bounded_wait_limit_is_checked():
+    import torch
+    from paper_2309_08079_gb300._lib import MPCG_EINVAL
+    s = solver()
+    st = torch.zeros(2, dtype=torch.int32, device="cuda")
+    for bad in (0.0, 2.0, float("nan")):
+        assert s.lib.mpcg_selftest_wait(s.h, 0, bad, st.data_ptr(), None) == MPCG_EINVAL
