@@ -514,6 +514,53 @@ __device__ __forceinline__ void gj_inverse_sym(T *M, T *out, int nx_rt, int t) {
     group_sync(G);
 }
 
+// The same inversion with compile-time NX <= 32, one row per lane in
+// registers: pivot j's scaled row is broadcast by shuffles, every other lane
+// updates its own row, then its column entry.  The element operations and
+// their order are those above (scale row j, M_ic -= M_ij M_jc, M_ij = -M_ij
+// d, M_jj = d); only the indexing, the shared-memory round trips and the
+// warp barriers of the loops are gone.  M is read and the symmetrised
+// inverse written through shared memory (both nx x nx, row-major).
+template <typename T, int NX>
+__device__ __forceinline__ void gj_inverse_sym_reg(T *M, T *out, int t) {
+    static_assert(NX >= 1 && NX <= 32, "one row per lane");
+    T row[NX];
+#pragma unroll
+    for (int c = 0; c < NX; ++c) row[c] = t < NX ? M[t * NX + c] : T(0);
+#pragma unroll
+    for (int j = 0; j < NX; ++j) {
+        const T d = T(1) / __shfl_sync(0xffffffffu, row[j], j);
+        if (t == j) {
+#pragma unroll
+            for (int c = 0; c < NX; ++c)
+                if (c != j) row[c] *= d;
+        }
+        T rj[NX];
+#pragma unroll
+        for (int c = 0; c < NX; ++c) rj[c] = __shfl_sync(0xffffffffu, row[c], j);
+        if (t != j) {
+            const T mij = row[j];
+#pragma unroll
+            for (int c = 0; c < NX; ++c)
+                if (c != j) row[c] -= mij * rj[c];
+            row[j] = -row[j] * d;
+        } else {
+            row[j] = d;
+        }
+    }
+    __syncwarp();  // every lane has read M
+    if (t < NX) {
+#pragma unroll
+        for (int c = 0; c < NX; ++c) M[t * NX + c] = row[c];
+    }
+    __syncwarp();
+    if (t < NX) {
+#pragma unroll
+        for (int c = 0; c < NX; ++c) out[t * NX + c] = T(0.5) * (M[t * NX + c] + M[c * NX + t]);
+    }
+    __syncwarp();
+}
+
 // Warp form of the fused formation (nx <= 16: one warp per knot).  A CTA
 // takes `kpb` consecutive knots plus one extra warp for the successor of its
 // last knot; after a CTA barrier, warp w forms Po[k] from its own Pd[k] and
@@ -590,7 +637,12 @@ form_fused_warp_kernel(const SchurArgs<T> a, T *Pd, T *Po, int kpb) {
             for (int e = t; e < n2; e += 32) Sd[e] = D[e];
         }
         __syncwarp();
-        gj_inverse_sym<T, NXC>(D, P, nx, t);
+        // float32: one row per lane (FP32 pipes are wide; measured 21 -> 16
+        // us at N = 512).  float64 keeps the 32-lane loops: each lane's row
+        // doubles the warp's FP64 instructions, and GB300's FP64 rate makes
+        // that the cost (measured 43 -> 51 us).
+        if constexpr (NXC > 0 && sizeof(T) == 4) gj_inverse_sym_reg<T, NXC>(D, P, t);
+        else gj_inverse_sym<T, NXC>(D, P, nx, t);
         if (!extra)
             for (int e = t; e < n2; e += 32) Pd[(size_t)kg * n2 + e] = P[e];
     }
