@@ -11,8 +11,8 @@ are timed on the device with CUDA events on the launching stream.
 
 Also measured in the same run and reported in the same JSON line:
   e2e        the same solve through the public API with host buffers: the
-             step's inputs copied from pinned host memory and the results
-             read back inside the timed region;
+             step's inputs copied from pinned host memory (one copy) and the
+             results read back (one copy) inside the timed region;
   batched    256 ragged instances (N_i ~ U{32..512}), 20 warm solves per
              instance captured in one CUDA graph, against the single-instance
              path looped over the same solves on the same GPU;
@@ -414,48 +414,32 @@ def run_ours(args, rank, world, local_rank):
 
 
 def run_e2e(s, lq, lam0, opts, dev, flush, steps, warmup):
-    """Same solve through the public API with host buffers: H2D of the
-    step's inputs (pinned), the four calls, D2H of lambda, dx, du, stats."""
+    """Same solve through the public API with host buffers: the step's inputs
+    (A..c and lambda0) staged in one pinned buffer and copied in with one
+    H2D copy, the three launches, and lambda, dx, du and the stats copied
+    back with one D2H copy (paper_2309_08079_gb300.staging.HostStaging)."""
     import torch
-    from paper_2309_08079_gb300.solver import LQTensors
+    from paper_2309_08079_gb300.staging import HostStaging
     stream = torch.cuda.current_stream()
-    host = {f: torch.from_numpy(np.ascontiguousarray(getattr(lq, f))).pin_memory()
-            for f in LQTensors.FIELDS}
-    lt = LQTensors.from_numpy(lq, device=dev)
-    sch = s.alloc_schur(lt)
-    stats = s.alloc_stats(1, dev)
-    lam_h = [t.cpu().pin_memory() for t in lam0[:warmup + steps]]
-    lam_d = torch.empty_like(lam0[0])
-    out_lam = torch.empty(lam_d.shape, dtype=lam_d.dtype).pin_memory()
-    dx_d = torch.empty(lq.N, lq.nx, device=dev)
-    du_d = torch.empty(lq.N - 1, lq.nu, device=dev)
-    dx_h = torch.empty(dx_d.shape).pin_memory()
-    du_h = torch.empty(du_d.shape).pin_memory()
-    st_h = torch.empty(24, dtype=torch.uint8).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in host.values()) + lam_h[0].numel() * 4
-    d2h = (out_lam.numel() + dx_h.numel() + du_h.numel()) * 4 + 24
+    stg = HostStaging(s, lq.nx, lq.nu, lq.N, device=dev)
+    stg.load(lq)
+    lam_h = [t.cpu().numpy() for t in lam0[:warmup + steps]]
     times = []
     for i in range(warmup + steps):
         flush.zero_()
+        stg.host["lam"][:] = lam_h[i]  # the controller's own host memory, before the timed region
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for f in LQTensors.FIELDS:
-            getattr(lt, f).copy_(host[f], non_blocking=True)
-        lam_d.copy_(lam_h[i], non_blocking=True)
-        s.form(lt, sch)
-        s.pcg_solve(lt, sch, lam_d, opts, stats)
-        s.recover_step(lt, lam_d, dx_d, du_d)
-        out_lam.copy_(lam_d, non_blocking=True)
-        dx_h.copy_(dx_d, non_blocking=True)
-        du_h.copy_(du_d, non_blocking=True)
-        st_h.copy_(stats, non_blocking=True)
+        stg.step(opts, stream)
         b.record(stream)
         b.synchronize()
         if i >= warmup:
             times.append(a.elapsed_time(b))
-    return {"value": float(np.mean(times)) * 1e3, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "steps": steps}
+    st = stg.read_stats()[0]
+    return {"value": float(np.mean(times)) * 1e3, "unit": UNIT, "h2d_bytes_per_step": int(stg.h2d_bytes),
+            "d2h_bytes_per_step": int(stg.d2h_bytes), "steps": steps, "copies_per_step": 2,
+            "last_status": int(st["status"])}
 
 
 def run_batched(s, dev, solves):

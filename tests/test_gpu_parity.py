@@ -435,3 +435,32 @@ def test_bounded_wait_limit_is_checked():
     st = torch.zeros(2, dtype=torch.int32, device="cuda")
     for bad in (0.0, 2.0, float("nan")):
         assert s.lib.mpcg_selftest_wait(s.h, 0, bad, st.data_ptr(), None) == MPCG_EINVAL
+
+
+# ------------------------------------------------------------------ host staging
+@pytest.mark.parametrize("N", [1, 2, 64, 512])
+def test_host_staging_matches_the_device_path(N):
+    """HostStaging (one H2D and one D2H copy per solve) returns what the
+    solve path returns on device-resident inputs, bit for bit (the same
+    kernels on the same data), and meets the parity bar; a second step with
+    new inputs overwrites everything."""
+    import torch
+    from paper_2309_08079_gb300.solver import make_opts
+    from paper_2309_08079_gb300.staging import HostStaging
+    s = solver()
+    stg = HostStaging(s, 14, 7, N)
+    for seed in (N + 11, N + 12):
+        lq = gen.kuka_lq(14, 7, N, seed).astype(np.float32)
+        stg.load(lq)
+        stg.host["lam"][:] = 0.0
+        stg.step(make_opts())
+        torch.cuda.synchronize()
+        lam, dx, du, st, _ = run_gpu(lq)
+        np.testing.assert_array_equal(stg.host["lam"], lam.astype(np.float32))
+        np.testing.assert_array_equal(stg.host["dx"], dx.astype(np.float32))
+        if N > 1:
+            np.testing.assert_array_equal(stg.host["du"], du.astype(np.float32))
+        hs = stg.read_stats()[0]
+        assert hs["status"] == 0 and hs["iters"] == st["iters"][0]
+        e_lam, e_dz, _ = parity(lq)
+        assert e_lam < TOL_F32 and e_dz < TOL_F32
