@@ -13,15 +13,36 @@ starts on a 256-byte boundary.
 """
 from __future__ import annotations
 
-from typing import Dict, Optional
+from typing import Dict
 
 import numpy as np
 import torch
 
 from . import _lib as L
-from .solver import LQTensors, SchurTensors, Solver
+from .solver import STATS_DTYPE, LQTensors, SchurTensors, Solver
 
 _ALIGN = 256
+_ORDER = ("A", "B", "Qd", "Rd", "q", "r", "c", "lam", "dx", "du", "stats")
+
+
+def layout(nx: int, nu: int, N: int, esz: int):
+    """Element offsets of one solve's arrays in the shared buffer.
+
+    Returns (shapes, offsets, total, in_end, out_begin, out_end): shapes and
+    offsets by name (order A, B, Qd, Rd, q, r, c, lam, dx, du, stats; each
+    offset a multiple of 256 bytes), the buffer length, the end of the input
+    prefix [0, in_end) and the output suffix [out_begin, out_end)."""
+    Kc = max(N - 1, 1)
+    shapes = {"A": (Kc, nx, nx), "B": (Kc, nx, nu), "Qd": (N, nx), "Rd": (Kc, nu),
+              "q": (N, nx), "r": (Kc, nu), "c": (N, nx), "lam": (N, nx), "dx": (N, nx),
+              "du": (Kc, nu), "stats": (L.STATS_BYTES // esz,)}
+    step = _ALIGN // esz
+    off, o = {}, 0
+    for name in _ORDER:
+        off[name] = o
+        o += -(-int(np.prod(shapes[name])) // step) * step
+    return (shapes, off, o, off["lam"] + N * nx, off["lam"],
+            off["stats"] + L.STATS_BYTES // esz)
 
 
 class HostStaging:
@@ -37,31 +58,19 @@ class HostStaging:
     def __init__(self, solver: Solver, nx: int, nu: int, N: int, dtype=torch.float32,
                  device="cuda"):
         self.s = solver
-        Kc = max(N - 1, 1)
         esz = torch.empty((), dtype=dtype).element_size()
-        shapes = [("A", (Kc, nx, nx)), ("B", (Kc, nx, nu)), ("Qd", (N, nx)), ("Rd", (Kc, nu)),
-                  ("q", (N, nx)), ("r", (Kc, nu)), ("c", (N, nx)), ("lam", (N, nx)),
-                  ("dx", (N, nx)), ("du", (Kc, nu)), ("stats", (L.STATS_BYTES // esz,))]
-        step = _ALIGN // esz
-        off, o = {}, 0
-        for name, shp in shapes:
-            off[name] = o
-            o += -(-int(np.prod(shp)) // step) * step
+        shapes, off, o, self.in_end, self.out_begin, self.out_end = layout(nx, nu, N, esz)
         self.numel = o
-        self.dev = torch.empty(o, dtype=dtype, device=device)
-        self.host_t = torch.empty(o, dtype=dtype).pin_memory()
-        self.host_t.zero_()
-        self.dev.zero_()
+        self.dev = torch.zeros(o, dtype=dtype, device=device)
+        self.host_t = torch.zeros(o, dtype=dtype).pin_memory()
         d: Dict[str, torch.Tensor] = {}
         self.host: Dict[str, np.ndarray] = {}
         hnp = self.host_t.numpy()
-        for name, shp in shapes:
+        for name in _ORDER:
+            shp = shapes[name]
             n = int(np.prod(shp))
             d[name] = self.dev[off[name]:off[name] + n].view(*shp)
             self.host[name] = hnp[off[name]:off[name] + n].reshape(shp)
-        self.in_end = off["lam"] + N * nx          # inputs and lambda0: [0, in_end)
-        self.out_begin = off["lam"]                 # results: [out_begin, out_end)
-        self.out_end = off["stats"] + L.STATS_BYTES // esz
         self.lq = LQTensors(nx, nu, N, *(d[f] for f in LQTensors.FIELDS), knot_off=None, nb=1,
                             total=N)
         self.lam, self.dx, self.du = d["lam"], d["dx"], d["du"]
@@ -96,5 +105,5 @@ class HostStaging:
                                                           non_blocking=True)
 
     def read_stats(self) -> np.ndarray:
-        return self.host["stats"].view(np.uint8).view(
-            np.dtype([("iters", "<i4"), ("status", "<i4"), ("eta", "<f8"), ("relres", "<f8")]))
+        """The stats records of the last completed step (host copy)."""
+        return self.host["stats"].view(np.uint8).view(STATS_DTYPE)

@@ -56,3 +56,19 @@ def test_cache_round_trip(tmp_path):
     assert d["k1"] == e and d["k2"]["plan"] == "single_auto"
     path.write_text("not json")
     assert t._load() == {}
+
+
+def test_step_plans_give_each_instance_its_own_cluster_size():
+    """The 32-knot step plan puts every instance in the group whose upper
+    edge is its horizon rounded up to a multiple of 32 (so the launch's
+    cluster holds ceil(N / 32) CTAs of 32 knots); the tiled-short variant
+    sends horizons up to a quarter of the longest class to the tiled kernel."""
+    Ns = gen.batch_horizons(256, 32, 512, 3)
+    plans = at.candidate_plans(Ns)
+    for g, i in at.group_instances(Ns, plans["steps32_auto"]):
+        assert g["hi"] % 32 == 0 and g["hi"] - g["lo"] == 32
+        assert np.all(-(-Ns[i] // 32) * 32 == g["hi"])
+    groups = at.group_instances(Ns, plans["steps64_tile_short"])
+    tiled = [(g, i) for g, i in groups if g["mode"] == 3]
+    assert len(tiled) == 1 and tiled[0][0]["hi"] == 128 and np.all(Ns[tiled[0][1]] <= 128)
+    assert all(g["mode"] == 0 and g["hi"] - g["lo"] == 64 for g, _ in groups if g["mode"] != 3)
