@@ -422,9 +422,10 @@ __global__ void axpy_kernel(int nx, BatchView bv, const T *__restrict__ d, T *__
 }
 
 // ---------------------------------------------------------------------------
-// Fused formation (diagonal costs): block row k of S+ and gamma_k (as
-// form_schur_kernel), Pd[k] = D_k^-1 (as precon_inv_kernel) and, when k has
-// a successor, Po[k] = -Pd[k+1] phi_k Pd[k] (as precon_off_kernel) in one
+// Fused formation (diagonal costs): block row k of S+ and gamma_k (Sec.
+// II-B, Eq. schur and Eq. trajoptSchur_1/2, as form_schur_kernel), Pd[k] =
+// D_k^-1 (Sec. IV-A, as precon_inv_kernel) and, when k has a successor,
+// Po[k] = -Pd[k+1] phi_k Pd[k] (Sec. IV-A, as precon_off_kernel) in one
 // launch, with no round trip through memory for the intermediate blocks.
 // The operations and their order are those of the three kernels; the values
 // agree with theirs to rounding (compile-time loop shapes let the compiler
