@@ -11,8 +11,13 @@
  *                                                          per-block form of
  *                                                          Algorithm 2)
  *   mpcg_recover_step  dz = -G^-1 (g - C^T lambda)        (Eq. schur)
- * plus two additions with no counterpart in the paper: batched (ragged
- * horizon) forms of every call and a backward (adjoint) pass.
+ *   mpcg_form_schur_precon  the first two in one launch
+ * plus additions with no counterpart in the paper: batched (ragged horizon)
+ * forms of every call, a backward (adjoint) pass, iterative refinement,
+ * comparison preconditioners (mpcg_opts.precon), and a diagnostic of the
+ * bounded device waits (mpcg_selftest_wait).  The outer loop's device
+ * pieces on a synthetic model follow at the end: linearisation (Sec. II-A
+ * Step 1) and the parallel line search (Sec. IV-C).
  *
  * Problem statement (Sec. II-A, Step 2).  N knot points, states
  * x_0..x_{N-1} (nx each), controls u_0..u_{N-2} (nu each).  G is diagonal:
