@@ -100,18 +100,20 @@ def candidate_plans(Ns: np.ndarray) -> Dict[str, List[dict]]:
         # power-of-two class's (an N = 260 instance takes 9 CTAs, not 16);
         # mixed cluster sizes on concurrent streams also fill the GPCs that
         # 16-CTA clusters leave partly idle
-        for step in (32, 64):
+        for step in (32, 64, 96, 128, 192):
             top = -(-int(np.max(Ns)) // step) * step
             bounds = list(range(step, top + 1, step))
             plans[f"steps{step}_auto"] = [{"lo": b - step, "hi": b, "mode": 0, "cluster": 0}
                                           for b in bounds]
-        # the same in 64-knot steps, the short horizons (a quarter of the
-        # longest or less) on the tiled CTA-per-instance kernel
+        # the same, the short horizons (a quarter of the longest class or
+        # less) on the tiled CTA-per-instance kernel
         if edges[-1] >= 256:
             cut = edges[-1] // 4
-            top = -(-int(np.max(Ns)) // 64) * 64
-            plans["steps64_tile_short"] = [{"lo": 0, "hi": cut, "mode": 3, "cluster": 0}] + [
-                {"lo": b - 64, "hi": b, "mode": 0, "cluster": 0} for b in range(cut + 64, top + 1, 64)]
+            for step in (32, 64):
+                top = max(cut, -(-int(np.max(Ns)) // step) * step)
+                plans[f"steps{step}_tile_short"] = [{"lo": 0, "hi": cut, "mode": 3, "cluster": 0}] + [
+                    {"lo": b - step, "hi": b, "mode": 0, "cluster": 0}
+                    for b in range(cut + step, top + 1, step)]
         # two halves of the horizon range
         mid = edges[-1] // 2
         if edges[0] <= mid:
