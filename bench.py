@@ -481,10 +481,11 @@ def run_batched(s, dev, solves):
                 s.pcg_solve(lt, sch, work[r], opts_m, stats[r], ws)
             s.recover_step(lt, work[r], dx, du)
 
-    # the autotuner times its candidate launch plans on the first warm start
-    # (a fresh cache, so every run tunes) and the chosen plan is graphed too
+    # the autotuner times its candidate launch plans on the first warm start,
+    # each captured in a CUDA graph as below (a fresh cache, so every run
+    # tunes), and the chosen plan is graphed too
     with tempfile.TemporaryDirectory() as td:
-        tuner = Autotuner(s, cache_path=os.path.join(td, "tune.json"), reps=3)
+        tuner = Autotuner(s, cache_path=os.path.join(td, "tune.json"), reps=3, graph=True)
         tuned = tuner.tune(lt, sch, master[0], opts)
         runner = tuner.runner(lt, sch, master[0], opts)
 

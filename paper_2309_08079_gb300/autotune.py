@@ -194,8 +194,13 @@ def _default_cache() -> str:
 class Autotuner:
     """Chooses, times and caches the launch plan of batched PCG solves."""
 
-    def __init__(self, solver: Solver, cache_path: Optional[str] = None, reps: int = 5):
+    def __init__(self, solver: Solver, cache_path: Optional[str] = None, reps: int = 5,
+                 graph: bool = False):
+        """graph=True times each plan captured in a CUDA graph (for callers
+        that replay graphs: concurrent branches of a graph have no launch
+        order, so a plan's longest-first start is not kept there)."""
         self.solver = solver
+        self.graph = bool(graph)
         self.cache_path = cache_path if cache_path is not None else _default_cache()
         self.reps = max(1, int(reps))
         self.last_timings: Dict[str, float] = {}
@@ -205,7 +210,7 @@ class Autotuner:
         p = torch.cuda.get_device_properties(lq.device)
         dt = {torch.float32: "f32", torch.float64: "f64"}[lq.dtype]
         return (f"{p.name}|sm{p.multi_processor_count}|{dt}|nx{lq.nx}|nu{lq.nu}|B{lq.nb}|"
-                f"{histogram_key(lq.Ns)}")
+                f"{histogram_key(lq.Ns)}" + ("|graph" if self.graph else ""))
 
     def _load(self) -> dict:
         try:
@@ -229,6 +234,8 @@ class Autotuner:
 
     # ---------------------------------------------------------------- tuning
     def _time(self, runner: PlanRunner, schur, lam0, lam, stats) -> float:
+        if self.graph:
+            return self._time_graph(runner, schur, lam0, lam, stats)
         times = []
         for r in range(self.reps + 1):
             lam.copy_(lam0)
@@ -241,6 +248,33 @@ class Autotuner:
             b.synchronize()
             if r:  # the first run chooses launch shapes
                 times.append(a.elapsed_time(b))
+        return float(np.median(times))
+
+    def _time_graph(self, runner: PlanRunner, schur, lam0, lam, stats) -> float:
+        dev = lam.device
+        lam.copy_(lam0)
+        runner.pcg_solve(schur, lam, stats)  # chooses launch shapes outside the capture
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                lam.copy_(lam0)
+                runner.pcg_solve(schur, lam, stats)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        times = []
+        for r in range(self.reps + 1):
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            g.replay()
+            b.record()
+            b.synchronize()
+            if r:
+                times.append(a.elapsed_time(b))
+        del g
         return float(np.median(times))
 
     def tune(self, lq: LQTensors, schur: SchurTensors, lam0: torch.Tensor, opts=None,
