@@ -133,6 +133,30 @@ def test_autotuner_tunes_caches_and_reuses(tmp_path):
     _check_lam(batch, lam.cpu().double().numpy(), read_stats(stats), los)
 
 
+def test_graph_mode_tuning_has_its_own_cache_entry(tmp_path):
+    """Autotuner(graph=True) times each plan captured in a CUDA graph; its
+    choice is cached under its own key (the eager entry is separate), and
+    the runner it returns solves the batch."""
+    import torch
+    from paper_2309_08079_gb300.autotune import Autotuner
+    from paper_2309_08079_gb300.solver import read_stats
+    Ns = gen.batch_horizons(24, 32, 300, 12)
+    s, batch, lt, sch, lam0 = _setup(Ns, 4500)
+    los = _oracle_lams(batch)
+    path = str(tmp_path / "tune.json")
+    g = Autotuner(s, cache_path=path, reps=1, graph=True)
+    best = g.tune(lt, sch, lam0, only=("single_auto", "classes_auto", "steps64_auto"))
+    assert best["plan"] in g.last_timings and all(t > 0 for t in g.last_timings.values())
+    assert g.key(lt).endswith("|graph")
+    assert g.cached_plan(lt)["plan"] == best["plan"]
+    assert Autotuner(s, cache_path=path, reps=1).cached_plan(lt) is None
+    lam = lam0.clone()
+    stats = s.alloc_stats(batch.B)
+    g.runner(lt, sch, lam0).pcg_solve(sch, lam, stats)
+    torch.cuda.synchronize()
+    _check_lam(batch, lam.cpu().double().numpy(), read_stats(stats), los)
+
+
 def test_plan_runner_in_a_cuda_graph():
     """A multi-stream plan captured in a CUDA graph gives the eager result."""
     import torch
