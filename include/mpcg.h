@@ -136,6 +136,22 @@ typedef struct {
        it stalls from N = 32 on; it exists to show why the paper symmetrises
        it).  Other values: MPCG_EINVAL. */
     int precon;
+    /* Backward calls only (mpcg_backward*): steps of iterative refinement of
+       the adjoint solve S+ mu = lambda_bar' (as mpcg_refine_step does for
+       the forward solve: the residual lambda_bar' - S+ mu formed in extended
+       precision from the inputs, not from the stored S+, a correction PCG
+       with the same S+ and Phi^-1, mu += correction).  0: none.  While they
+       run, grads->q and grads->c serve as the correction's scratch; both
+       receive their gradients afterwards.  Ignored by the other calls;
+       negative: MPCG_EINVAL. */
+    int refine;
+    /* Accumulation of the PCG dot products for float32 (dtype 0):
+       0 float pairs ("double-float": exact products by FMA, TwoSum
+       additions, ~44 significant bits; the default), 1 float64 (products
+       and every partial sum in FP64 instructions; slower on GB300, whose
+       FP64 pipe is a small fraction of its FP32 rate).  float64 always
+       accumulates in float64.  Other values: MPCG_EINVAL. */
+    int dot;
 } mpcg_opts;
 
 typedef struct {

@@ -4,12 +4,14 @@ Forward runs the fused form_schur + form_precon, pcg_solve and recover_step; it 
 only S+, Phi^-1 (Sd, So, Pd, Po) and the solution (lambda, dx, du) besides
 the inputs.  Backward runs the library's adjoint: a second PCG solve on the
 same S+ with the same preconditioner, then per-knot outer products (see
-mpcg_backward in include/mpcg.h).
+mpcg_backward in include/mpcg.h).  cfg["refine"] refinement steps follow
+the forward solve and, through opts.refine, the adjoint solve.
 """
 from __future__ import annotations
 
 import torch
 
+from . import _lib as L
 from .solver import LQTensors, SchurTensors, make_opts
 
 
@@ -30,7 +32,9 @@ class MPCGSolve(torch.autograd.Function):
                                             refine=int(cfg.get("refine", 0)))
         ctx.lq_meta = (lq.nx, lq.nu, lq.N, lq.knot_off, lq.nb, lq.total)
         ctx.solver = s
-        ctx.opts = opts
+        bopts = L.mpcg_opts.from_buffer_copy(opts)
+        bopts.refine = int(cfg.get("refine", 0))
+        ctx.opts = bopts
         ctx.workspace = cfg.get("workspace")
         ctx.save_for_backward(lq.A, lq.B, lq.Qd, lq.Rd, lq.q, lq.r, lq.c, schur.Sd, schur.So,
                               schur.Pd, schur.Po, schur.gamma, schur.info, lam, dx, du)

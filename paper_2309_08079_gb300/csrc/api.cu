@@ -133,6 +133,7 @@ template <typename T>
 int choose_pcg_cluster(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, PcgLaunch &L,
                        bool wide = false) {
     L.cta_mode = 0;
+    L.dot = (std::is_same<T, float>::value && o && o->dot == 1) ? 1 : 0;
     const int nx = d.nx;
     if (wide && nx > 16) return MPCG_EUNSUPPORTED;
     const bool reg = !wide && std::is_same<T, float>::value && nx == 14;
@@ -167,10 +168,10 @@ int choose_pcg_cluster(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opt
         const int W = L.threads / 32;
         L.stage = 0;
         if (L.mode == MODE_PTR) {
-            size_t with = pcg_smem_bytes<T>(L.kpc_max, L.vs, C, W, nx, 1);
+            size_t with = pcg_smem_bytes<T>(L.kpc_max, L.vs, C, W, nx, 1, L.dot);
             if (with <= (size_t)h->smem_optin) L.stage = 1;
         }
-        L.smem = pcg_smem_bytes<T>(L.kpc_max, L.vs, C, W, nx, L.stage);
+        L.smem = pcg_smem_bytes<T>(L.kpc_max, L.vs, C, W, nx, L.stage, L.dot);
         const int active = pcg_max_clusters<T>(L);
         if (active >= 1) {
             L.clusters = std::max(1, std::min(B, active));
@@ -192,6 +193,12 @@ template <typename T>
 int choose_pcg(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, const mpcg_schur *s,
                PcgLaunch &L) {
     const int mode = o ? o->mode : 0;
+    // float64 accumulation of float32 dot products exists in the cluster
+    // kernel only
+    if (std::is_same<T, float>::value && o && o->dot == 1) {
+        if (mode == 2 || mode == 3) return MPCG_EUNSUPPORTED;
+        return choose_pcg_cluster<T>(h, d, B, o, L, mode == 4);
+    }
     if (mode == 2) return choose_pcg_cta<T>(h, d, B, L);
     if (mode == 3) {
         if (choose_pcg_tile<T>(h, d, B, s, L) == MPCG_OK) return MPCG_OK;
@@ -242,6 +249,7 @@ template <typename T>
 int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const mpcg_schur *s,
           const T *rhs, T sign, T *lam, const mpcg_opts *o, mpcg_stats *stats, void *ws,
           cudaStream_t st) {
+    if (o && (o->refine < 0 || o->dot < 0 || o->dot > 1)) return MPCG_EINVAL;
     PcgLaunch L{};
     int rc = MPCG_OK;
     {
@@ -250,7 +258,8 @@ int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const 
         const int aligned = (((uintptr_t)s->Sd | (uintptr_t)s->So | (uintptr_t)s->Pd | (uintptr_t)s->Po) % 16) == 0;
         const int tickets = (o && o->instances && o->n_instances > 0) ? o->n_instances : B;
         auto key = std::make_tuple(d.dtype, d.nx, d.N, tickets,
-                                   (o ? o->cluster : 0) | ((o ? o->mode : 0) << 8) | (aligned << 16));
+                                   (o ? o->cluster : 0) | ((o ? o->mode : 0) << 8) | (aligned << 16) |
+                                       ((o ? o->dot : 0) << 17));
         auto it = h->shapes.find(key);
         if (it != h->shapes.end()) {
             L = it->second;
@@ -310,6 +319,23 @@ int backward_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, c
     if (rc) return rc;
     rc = pcg_t<T>(h, d, B, knot_off, s, lbar, T(1), mu, o, stats, ws, st);
     if (rc) return rc;
+    // Refinement of the adjoint solve: res = lambda_bar' - S+ mu formed from
+    // the inputs (resid_kernel with g = 0 and the seed as -c), a correction
+    // solve S+ delta = res from delta = 0, mu += delta.  g->c and g->q (both
+    // [K][nx]) hold res and delta until their gradients overwrite them.
+    const int nref = o ? o->refine : 0;
+    for (int i = 0; i < nref; ++i) {
+        T *res = (T *)g->c, *delta = (T *)g->q;
+        rc = err_cuda(launch_resid<T>(d.nx, d.nu, bv, Kgrid, A, Bm, Qd, Rd, nullptr, nullptr, lbar,
+                                      T(-1), mu, res, st));
+        if (rc) return rc;
+        rc = err_cuda(cudaMemsetAsync(delta, 0, (size_t)Kgrid * d.nx * sizeof(T), st));
+        if (rc) return rc;
+        rc = pcg_t<T>(h, d, B, knot_off, s, res, T(1), delta, o, nullptr, ws, st);
+        if (rc) return rc;
+        rc = err_cuda(launch_axpy<T>(d.nx, bv, Kgrid, delta, mu, st));
+        if (rc) return rc;
+    }
     rc = err_cuda(launch_recover<T>(d.nx, d.nu, bv, Kgrid, A, Bm, Qd, Rd, dx_bar, du_bar, mu,
                                     (T *)g->q, (T *)g->r, st));
     if (rc) return rc;
@@ -397,7 +423,7 @@ int refine_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, con
     T *delta = (T *)(w + 256 + vec);
     int rc = err_cuda(launch_resid<T>(d.nx, d.nu, bv, Kgrid, (const T *)lq->A, (const T *)lq->B,
                                       (const T *)lq->Qd, (const T *)lq->Rd, (const T *)lq->q,
-                                      (const T *)lq->r, (const T *)lq->c, lam, res, st));
+                                      (const T *)lq->r, (const T *)lq->c, T(1), lam, res, st));
     if (rc) return rc;
     rc = err_cuda(cudaMemsetAsync(delta, 0, (size_t)Kgrid * d.nx * sizeof(T), st));
     if (rc) return rc;
@@ -564,7 +590,7 @@ int mpcg_backward_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_of
                           mpcg_stats *stats, void *workspace, void *stream) {
     if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !lambda || !dx ||
         !lam_bar || !dx_bar || !g || !g->A || !g->B || !g->Qd || !g->Rd || !g->q || !g->r ||
-        !g->c || !workspace || (d.N > 1 && (!du || !du_bar)))
+        !g->c || !workspace || (d.N > 1 && (!du || !du_bar)) || (opts && opts->refine < 0))
         return MPCG_EINVAL;
     if (lq->Q) return MPCG_EUNSUPPORTED;  // gradients are stated for diagonal costs
     if (d.dtype == 1)
@@ -633,7 +659,7 @@ extern "C" int mpcg_backward_batched_noalloc(mpcg_handle *h, mpcg_dims d, int B,
                                              void *stream) {
     if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !lambda || !dx ||
         !lam_bar || !dx_bar || !g || !g->A || !g->B || !g->Qd || !g->Rd || !g->q || !g->r ||
-        !g->c || (d.N > 1 && (!du || !du_bar)))
+        !g->c || (d.N > 1 && (!du || !du_bar)) || (opts && opts->refine < 0))
         return MPCG_EINVAL;
     if (lq->Q) return MPCG_EUNSUPPORTED;  // gradients are stated for diagonal costs
     const size_t need = mpcg_workspace_bytes(d, B);

@@ -116,6 +116,25 @@ struct Acc<double> {
     __device__ static __forceinline__ double div_x(double x, double b) { return x / b; }
 };
 
+// float32 storage with float64 accumulation (mpcg_opts.dot = 1): products of
+// two floats are exact in double, partial sums are rounded FP64 additions;
+// the iteration's scalars are still taken in float.
+struct AccF64 {
+    using type = double;
+    __device__ static __forceinline__ double zero() { return 0.0; }
+    __device__ static __forceinline__ double prod(float a, float b) {
+        return __dmul_rn((double)a, (double)b);
+    }
+    __device__ static __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ static __forceinline__ double add_tree(double a, double b) { return __dadd_rn(a, b); }
+    __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    __device__ static __forceinline__ double shfl_xor(double a, int m) {
+        return __shfl_xor_sync(0xffffffffu, a, m);
+    }
+    __device__ static __forceinline__ double to_double(double a) { return a; }
+    __device__ static __forceinline__ float to_T(double a) { return __double2float_rn(a); }
+};
+
 template <typename T>
 __device__ __forceinline__ T fma_rn(T a, T b, T c);
 template <>

@@ -351,12 +351,15 @@ grad_kernel(int nx, int nu, BatchView bv, const T *__restrict__ lam,
 // the PCG recurrences.  Block row k:
 //   k = 0: -(dx_0 + c_0)
 //   k > 0: A_{k-1} dx_{k-1} + B_{k-1} du_{k-1} - dx_k - c_k
+// With q = r = nullptr (g = 0) and c scaled by csign = -1 the same kernel
+// forms v - S+ mu = v - C G^-1 C^T mu for any right-hand side v (passed as
+// c): the residual of the adjoint solve of the backward pass.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(FORM_THREADS)
 resid_kernel(int nx, int nu, BatchView bv, const T *__restrict__ A, const T *__restrict__ B,
              const T *__restrict__ Qd, const T *__restrict__ Rd, const T *__restrict__ q,
-             const T *__restrict__ r, const T *__restrict__ c, const T *__restrict__ lam,
+             const T *__restrict__ r, const T *__restrict__ c, T csign, const T *__restrict__ lam,
              T *__restrict__ out) {
     using AT = Acc<T>;
     using X = typename AT::type;
@@ -376,7 +379,7 @@ resid_kernel(int nx, int nu, BatchView bv, const T *__restrict__ A, const T *__r
     // dz entries of this knot (dx_k) and of the previous one (dx_{k-1}, du_{k-1})
     for (int i = t; i < nx; i += G) {
         X s = AT::from(lam[(size_t)kg * nx + i]);
-        s = AT::add(s, AT::from(-q[(size_t)kg * nx + i]));
+        if (q) s = AT::add(s, AT::from(-q[(size_t)kg * nx + i]));
         if (!last) {
             const T *Ak = A + (size_t)(kg - b) * nx * nx;
             for (int m = 0; m < nx; ++m) s = AT::add(s, AT::prod(-Ak[m * nx + i], lam[(size_t)(kg + 1) * nx + m]));
@@ -389,19 +392,19 @@ resid_kernel(int nx, int nu, BatchView bv, const T *__restrict__ A, const T *__r
         const T *Bp = B + (size_t)j * nx * nu;
         for (int i = t; i < nx; i += G) {
             X s = AT::from(lam[(size_t)(kg - 1) * nx + i]);
-            s = AT::add(s, AT::from(-q[(size_t)(kg - 1) * nx + i]));
+            if (q) s = AT::add(s, AT::from(-q[(size_t)(kg - 1) * nx + i]));
             for (int m = 0; m < nx; ++m) s = AT::add(s, AT::prod(-Ap[m * nx + i], lam[(size_t)kg * nx + m]));
             dx_prev[i] = AT::div_x(s, Qd[(size_t)(kg - 1) * nx + i]);
         }
         for (int i = t; i < nu; i += G) {
-            X s = AT::from(-r[(size_t)j * nu + i]);
+            X s = AT::from(r ? -r[(size_t)j * nu + i] : T(0));
             for (int m = 0; m < nx; ++m) s = AT::add(s, AT::prod(-Bp[m * nu + i], lam[(size_t)kg * nx + m]));
             du_prev[i] = AT::div_x(s, Rd[(size_t)j * nu + i]);
         }
     }
     group_sync(G);
     for (int i = t; i < nx; i += G) {
-        X s = AT::add(AT::neg(dx_cur[i]), AT::from(-c[(size_t)kg * nx + i]));
+        X s = AT::add(AT::neg(dx_cur[i]), AT::from(-csign * c[(size_t)kg * nx + i]));
         if (k > 0) {
             const int j = kg - b - 1;
             const T *Ap = A + (size_t)j * nx * nx;
@@ -968,12 +971,12 @@ cudaError_t launch_grad(int nx, int nu, BatchView bv, int Kgrid, const T *lam, c
 
 template <typename T>
 cudaError_t launch_resid(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B, const T *Qd,
-                         const T *Rd, const T *q, const T *r, const T *c, const T *lam, T *out,
-                         cudaStream_t s) {
+                         const T *Rd, const T *q, const T *r, const T *c, T csign, const T *lam,
+                         T *out, cudaStream_t s) {
     using X = typename Acc<T>::type;
     const int groups = FORM_THREADS / group_size(nx);
     resid_kernel<T><<<form_grid(nx, Kgrid), FORM_THREADS, sizeof(X) * (2 * nx + nu) * groups, s>>>(
-        nx, nu, bv, A, B, Qd, Rd, q, r, c, lam, out);
+        nx, nu, bv, A, B, Qd, Rd, q, r, c, csign, lam, out);
     return cudaGetLastError();
 }
 
@@ -1023,7 +1026,7 @@ cudaError_t form_prepare(int smem_optin) {
                                         T *, T *, T *, cudaStream_t);                             \
     template cudaError_t launch_resid<T>(int, int, BatchView, int, const T *, const T *,          \
                                          const T *, const T *, const T *, const T *, const T *,   \
-                                         const T *, T *, cudaStream_t);                           \
+                                         T, const T *, T *, cudaStream_t);                        \
     template cudaError_t launch_axpy<T>(int, BatchView, int, const T *, T *, cudaStream_t);     \
     template cudaError_t launch_form_fused<T>(const SchurArgs<T> &, T *, T *, int, cudaStream_t); \
     template size_t form_fused_smem_bytes<T>(int, int, int, int);                                \

@@ -52,6 +52,7 @@ struct PcgLaunch {
     int vw;        // pcg_tile_kernel: elements per shared-memory row load (2 or 4)
     int depth;     // pcg_tile_kernel: steps each knot stream copies ahead (1..4)
     int nxc;       // pcg_tile_kernel: nx fixed at compile time (14, 36), else 0
+    int dot;       // float32 only: 1 accumulates the dot products in float64 (AccF64)
     size_t smem;
 };
 
@@ -77,8 +78,8 @@ cudaError_t launch_grad(int nx, int nu, BatchView bv, int Kgrid, const T *lam, c
                         T *gRd, T *gc, cudaStream_t s);
 template <typename T>
 cudaError_t launch_resid(int nx, int nu, BatchView bv, int Kgrid, const T *A, const T *B, const T *Qd,
-                         const T *Rd, const T *q, const T *r, const T *c, const T *lam, T *out,
-                         cudaStream_t s);
+                         const T *Rd, const T *q, const T *r, const T *c, T csign, const T *lam,
+                         T *out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_axpy(int nx, BatchView bv, int Kgrid, const T *d, T *lam, cudaStream_t s);
 template <typename T> cudaError_t pcg_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
@@ -93,6 +94,6 @@ template <typename T> size_t pcg_cta_smem_bytes(int nmax, int vs, int W);
 template <typename T> cudaError_t pcg_cta_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
 template <typename T> int pcg_cta_max_blocks(const PcgLaunch &);
 cudaError_t form_prepare(int smem_optin);
-template <typename T> size_t pcg_smem_bytes(int kpc_max, int vs, int C, int W, int nx, int stage);
+template <typename T> size_t pcg_smem_bytes(int kpc_max, int vs, int C, int W, int nx, int stage, int dot);
 
 }  // namespace mpcg

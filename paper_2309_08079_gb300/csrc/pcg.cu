@@ -32,8 +32,9 @@
 // scalar decisions (alpha, beta, exit).
 //
 // Dot products: exact float products accumulated as float pairs (see
-// common.cuh); ||r||^2, used only by the exit test, is a sum of squares and
-// is accumulated in plain working precision.
+// common.cuh), or in float64 (mpcg_opts.dot = 1, the AccF64 policy); ||r||^2,
+// used only by the exit test, is a sum of squares and is accumulated in
+// plain working precision (in float64 with float64 accumulators).
 #include <type_traits>
 
 #include "pcg_rows.cuh"
@@ -42,10 +43,10 @@ namespace mpcg {
 
 constexpr int CMAX = 16;
 
-template <typename T>
-struct PayB;  // payload of exchange B: (r^T r~, ||r||^2)
+template <typename A>
+struct PayB;  // payload of exchange B: (r^T r~, ||r||^2), by accumulator type
 template <>
-struct PayB<float> {
+struct PayB<dfloat> {
     dfloat eta;
     float rr, pad;
 };
@@ -54,14 +55,18 @@ struct PayB<double> {
     double eta, rr;
 };
 
+// ||r||^2 += r_i^2 in the payload's precision
+__device__ __forceinline__ float rr_acc(float r, float acc) { return __fmaf_rn(r, r, acc); }
+__device__ __forceinline__ double rr_acc(float r, double acc) { return __fma_rn((double)r, (double)r, acc); }
+__device__ __forceinline__ double rr_acc(double r, double acc) { return __fma_rn(r, r, acc); }
+
 // Shared-memory carve-up (dynamic).  Slot arrays hold one partial per
 // (source CTA, source warp).  Offsets in bytes, computed identically
-// on the host (pcg_smem_bytes) and the device.
-template <typename T>
+// on the host (pcg_smem_bytes) and the device.  A: accumulator type.
+template <typename T, typename A>
 struct SmemLayout {
     size_t vecP, vecR, haloA, haloB, slotA, slotB, mbar, misc, mats, total;
     __host__ __device__ SmemLayout(int kpc_max, int vs, int W, int nx, int stage) {
-        using A = typename std::conditional<sizeof(T) == 4, dfloat, double>::type;
         size_t o = 0;
         auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
         vecP = o; o = al(o + sizeof(T) * (kpc_max + 2) * vs);
@@ -69,7 +74,7 @@ struct SmemLayout {
         haloA = o; o = al(o + sizeof(T) * 2 * vs);
         haloB = o; o = al(o + sizeof(T) * 2 * vs);
         slotA = o; o = al(o + sizeof(A) * CMAX * W);
-        slotB = o; o = al(o + sizeof(PayB<T>) * CMAX * W);
+        slotB = o; o = al(o + sizeof(PayB<A>) * CMAX * W);
         mbar = o; o = al(o + 2 * sizeof(uint64_t));
         misc = o; o = al(o + 16);
         mats = o;
@@ -126,28 +131,35 @@ __device__ __forceinline__ float resid_reg(float b, const float (&d)[NXR], const
     return __fadd_rn(a.hi, a.lo);
 }
 
-template <typename T>
-__device__ __forceinline__ PayB<T> payb_add(const PayB<T> &x, const PayB<T> &y) {
-    PayB<T> r;
-    r.eta = Acc<T>::add_tree(x.eta, y.eta);
+__device__ __forceinline__ dfloat acc_add_tree(dfloat a, dfloat b) { return df_add_lazy(a, b); }
+__device__ __forceinline__ double acc_add_tree(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ dfloat acc_shfl(dfloat a, int m) {
+    return dfloat{__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+}
+__device__ __forceinline__ double acc_shfl(double a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
+
+template <typename A>
+__device__ __forceinline__ PayB<A> payb_add(const PayB<A> &x, const PayB<A> &y) {
+    PayB<A> r;
+    r.eta = acc_add_tree(x.eta, y.eta);
     r.rr = x.rr + y.rr;
-    if constexpr (sizeof(T) == 4) r.pad = 0.f;
+    if constexpr (std::is_same<A, dfloat>::value) r.pad = 0.f;
     return r;
 }
-template <typename T>
-__device__ __forceinline__ PayB<T> payb_shfl(const PayB<T> &x, int m) {
-    PayB<T> r;
-    r.eta = Acc<T>::shfl_xor(x.eta, m);
+template <typename A>
+__device__ __forceinline__ PayB<A> payb_shfl(const PayB<A> &x, int m) {
+    PayB<A> r;
+    r.eta = acc_shfl(x.eta, m);
     r.rr = __shfl_xor_sync(0xffffffffu, x.rr, m);
-    if constexpr (sizeof(T) == 4) r.pad = 0.f;
+    if constexpr (std::is_same<A, dfloat>::value) r.pad = 0.f;
     return r;
 }
-template <typename T>
-__device__ __forceinline__ PayB<T> payb_zero() {
-    PayB<T> r;
-    r.eta = Acc<T>::zero();
-    r.rr = T(0);
-    if constexpr (sizeof(T) == 4) r.pad = 0.f;
+template <typename A>
+__device__ __forceinline__ PayB<A> payb_zero() {
+    PayB<A> r;
+    r.eta = A{};
+    r.rr = 0;
+    if constexpr (std::is_same<A, dfloat>::value) r.pad = 0.f;
     return r;
 }
 __device__ __forceinline__ void st_async_pay(uint32_t addr, const dfloat &v, uint32_t mbar) {
@@ -156,7 +168,7 @@ __device__ __forceinline__ void st_async_pay(uint32_t addr, const dfloat &v, uin
 __device__ __forceinline__ void st_async_pay(uint32_t addr, const double &v, uint32_t mbar) {
     st_async(addr, v, mbar);
 }
-__device__ __forceinline__ void st_async_pay(uint32_t addr, const PayB<float> &v, uint32_t mbar) {
+__device__ __forceinline__ void st_async_pay(uint32_t addr, const PayB<dfloat> &v, uint32_t mbar) {
     st_async_v4(addr, v.eta.hi, v.eta.lo, v.rr, 0.f, mbar);
 }
 __device__ __forceinline__ void st_async_pay(uint32_t addr, const PayB<double> &v, uint32_t mbar) {
@@ -168,11 +180,10 @@ __device__ __forceinline__ void st_async_pay(uint32_t addr, const PayB<double> &
 template <int MODE>
 constexpr int pcg_max_threads() { return MODE == MODE_REG ? 256 : 512; }
 
-template <typename T, int MODE, int LPK, int RPT>
+template <typename T, typename AT, int MODE, int LPK, int RPT>
 __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel(const PcgParams<T> P) {
-    using AT = Acc<T>;
     using A = typename AT::type;
-    using PB = PayB<T>;
+    using PB = PayB<A>;
     extern __shared__ __align__(16) unsigned char smem[];
 
     const uint32_t C = cluster_size();
@@ -186,7 +197,7 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
     const int nx = P.nx;
     const int vs = P.vs;
 
-    SmemLayout<T> L(P.kpc_max, vs, W, nx, P.stage_smem);
+    SmemLayout<T, A> L(P.kpc_max, vs, W, nx, P.stage_smem);
     T *vecP = reinterpret_cast<T *>(smem + L.vecP);
     T *vecR = reinterpret_cast<T *>(smem + L.vecR);
     T *haloA = reinterpret_cast<T *>(smem + L.haloA);  // [0, vs): left nbr's last knot; [vs, 2vs): right nbr's first
@@ -393,7 +404,7 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
         // Exchange B: cluster sums of (r^T r~, ||r||^2), same pattern.
         auto exchangeB = [&](PB v) -> PB {
 #pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) v = payb_add<T>(v, payb_shfl<T>(v, m));
+            for (int m = 16; m >= 1; m >>= 1) v = payb_add<A>(v, payb_shfl<A>(v, m));
             if (lane < C) st_async_pay(slotB_peer, v, mbB_peer);
             int fail = 0;
             if (tid == 0) {
@@ -402,10 +413,10 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
             }
             phB ^= 1u;
             if (__syncthreads_or(fail)) timed_out = true;
-            PB t = payb_zero<T>();
-            for (int q = lane; q < nslots; q += 32) t = payb_add<T>(t, slotB[q]);
+            PB t = payb_zero<A>();
+            for (int q = lane; q < nslots; q += 32) t = payb_add<A>(t, slotB[q]);
 #pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) t = payb_add<T>(t, payb_shfl<T>(t, m));
+            for (int m = 16; m >= 1; m >>= 1) t = payb_add<A>(t, payb_shfl<A>(t, m));
             return t;
         };
 
@@ -469,18 +480,18 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
                 __syncthreads();
                 T rt[RPT];
                 matvec(true, vecR, rt);
-                PB s2 = payb_zero<T>();
+                PB s2 = payb_zero<A>();
 #pragma unroll
                 for (int m = 0; m < RPT; ++m) {
                     s2.eta = AT::add(s2.eta, AT::prod(r_r[m], rt[m]));
-                    s2.rr = fma_rn(r_r[m], r_r[m], s2.rr);
+                    s2.rr = rr_acc(r_r[m], s2.rr);
                     p_r[m] = rt[m];
                     if (rx[m]) vecP[(kl + 1) * vs + rows[m]] = rt[m];
                 }
                 push_halo(hB_l, mbB_l, hB_r, mbB_r, rt);
                 s2 = exchangeB(s2);
                 eta = s2.eta;
-                rr_t = s2.rr;
+                rr_t = (T)s2.rr;
             }
             if (!timed_out) {
                 if (kl == 0 && has_left)
@@ -550,11 +561,11 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
                     // ---- r~ = Phi^-1 r; eta' = r^T r~, ||r||^2 ----------------------
                     T rt[RPT];
                     matvec(true, vecR, rt);
-                    PB s2 = payb_zero<T>();
+                    PB s2 = payb_zero<A>();
 #pragma unroll
                     for (int m = 0; m < RPT; ++m) {
                         s2.eta = AT::add(s2.eta, AT::prod(r_r[m], rt[m]));
-                        s2.rr = fma_rn(r_r[m], r_r[m], s2.rr);
+                        s2.rr = rr_acc(r_r[m], s2.rr);
                     }
                     push_halo(hB_l, mbB_l, hB_r, mbB_r, rt);
                     s2 = exchangeB(s2);
@@ -563,7 +574,7 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
                         break;
                     }
                     const T etan = AT::to_T(s2.eta);
-                    rr_t = s2.rr;
+                    rr_t = (T)s2.rr;
                     eta = s2.eta;
                     if (!isfinite(etan) || !isfinite(rr_t)) {
                         status = MPCG_NONFINITE;
@@ -620,20 +631,29 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
 // Host-side launch helpers (called from api.cu).
 // ---------------------------------------------------------------------------
 template <typename T>
-size_t pcg_smem_bytes(int kpc_max, int vs, int C, int W, int nx, int stage) {
+size_t pcg_smem_bytes(int kpc_max, int vs, int C, int W, int nx, int stage, int dot) {
     (void)C;
-    return SmemLayout<T>(kpc_max, vs, W, nx, stage).total;
+    if (sizeof(T) == 4 && !dot) return SmemLayout<T, dfloat>(kpc_max, vs, W, nx, stage).total;
+    return SmemLayout<T, double>(kpc_max, vs, W, nx, stage).total;
+}
+
+template <typename T, typename AT>
+static void (*pcg_fn_acc(const PcgLaunch &L))(const PcgParams<T>) {
+    if constexpr (sizeof(T) == 4) {
+        if (L.mode == MODE_REG) return pcg_cluster_kernel<float, AT, MODE_REG, 8, 2>;
+    }
+    if (L.lpk == 8) return pcg_cluster_kernel<T, AT, MODE_PTR, 8, 2>;
+    if (L.lpk == 16) return pcg_cluster_kernel<T, AT, MODE_PTR, 16, 1>;
+    if (L.rpt == 1) return pcg_cluster_kernel<T, AT, MODE_PTR, 32, 1>;
+    return pcg_cluster_kernel<T, AT, MODE_PTR, 32, 2>;
 }
 
 template <typename T>
 static void (*pcg_fn(const PcgLaunch &L))(const PcgParams<T>) {
     if constexpr (sizeof(T) == 4) {
-        if (L.mode == MODE_REG) return pcg_cluster_kernel<float, MODE_REG, 8, 2>;
+        if (L.dot) return pcg_fn_acc<float, AccF64>(L);
     }
-    if (L.lpk == 8) return pcg_cluster_kernel<T, MODE_PTR, 8, 2>;
-    if (L.lpk == 16) return pcg_cluster_kernel<T, MODE_PTR, 16, 1>;
-    if (L.rpt == 1) return pcg_cluster_kernel<T, MODE_PTR, 32, 1>;
-    return pcg_cluster_kernel<T, MODE_PTR, 32, 2>;
+    return pcg_fn_acc<T, Acc<T>>(L);
 }
 
 template <typename T>
@@ -674,17 +694,23 @@ static cudaError_t prepare_one(void (*fn)(const PcgParams<T>), int smem_optin) {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
+template <typename T, typename AT>
+static cudaError_t prepare_acc(int smem_optin) {
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+        if ((e = prepare_one<T>(pcg_cluster_kernel<T, AT, MODE_REG, 8, 2>, smem_optin))) return e;
+    }
+    if ((e = prepare_one<T>(pcg_cluster_kernel<T, AT, MODE_PTR, 8, 2>, smem_optin))) return e;
+    if ((e = prepare_one<T>(pcg_cluster_kernel<T, AT, MODE_PTR, 16, 1>, smem_optin))) return e;
+    if ((e = prepare_one<T>(pcg_cluster_kernel<T, AT, MODE_PTR, 32, 1>, smem_optin))) return e;
+    return prepare_one<T>(pcg_cluster_kernel<T, AT, MODE_PTR, 32, 2>, smem_optin);
+}
+
 cudaError_t pcg_prepare(int smem_optin) {
     cudaError_t e;
-    if ((e = prepare_one<float>(pcg_cluster_kernel<float, MODE_REG, 8, 2>, smem_optin))) return e;
-    if ((e = prepare_one<float>(pcg_cluster_kernel<float, MODE_PTR, 8, 2>, smem_optin))) return e;
-    if ((e = prepare_one<double>(pcg_cluster_kernel<double, MODE_PTR, 8, 2>, smem_optin))) return e;
-    if ((e = prepare_one<float>(pcg_cluster_kernel<float, MODE_PTR, 16, 1>, smem_optin))) return e;
-    if ((e = prepare_one<float>(pcg_cluster_kernel<float, MODE_PTR, 32, 1>, smem_optin))) return e;
-    if ((e = prepare_one<float>(pcg_cluster_kernel<float, MODE_PTR, 32, 2>, smem_optin))) return e;
-    if ((e = prepare_one<double>(pcg_cluster_kernel<double, MODE_PTR, 16, 1>, smem_optin))) return e;
-    if ((e = prepare_one<double>(pcg_cluster_kernel<double, MODE_PTR, 32, 1>, smem_optin))) return e;
-    return prepare_one<double>(pcg_cluster_kernel<double, MODE_PTR, 32, 2>, smem_optin);
+    if ((e = prepare_acc<float, Acc<float>>(smem_optin))) return e;
+    if ((e = prepare_acc<float, AccF64>(smem_optin))) return e;
+    return prepare_acc<double, Acc<double>>(smem_optin);
 }
 
 // Largest number of co-resident clusters of this shape (0 if it cannot run).
@@ -713,7 +739,7 @@ template cudaError_t pcg_launch<float>(const PcgLaunch &, const PcgParams<float>
 template cudaError_t pcg_launch<double>(const PcgLaunch &, const PcgParams<double> &, cudaStream_t);
 template int pcg_max_clusters<float>(const PcgLaunch &);
 template int pcg_max_clusters<double>(const PcgLaunch &);
-template size_t pcg_smem_bytes<float>(int, int, int, int, int, int);
-template size_t pcg_smem_bytes<double>(int, int, int, int, int, int);
+template size_t pcg_smem_bytes<float>(int, int, int, int, int, int, int);
+template size_t pcg_smem_bytes<double>(int, int, int, int, int, int, int);
 
 }  // namespace mpcg

@@ -46,12 +46,34 @@ def test_binding_declares_every_export(lib_path):
     assert len(set(msgs.values())) == len(msgs)
 
 
-def test_struct_layouts_match_header(lib_path):
+def test_struct_layouts_match_header(lib_path, tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets a
+    C compiler gives the header's struct."""
+    import shutil
+    import subprocess
     from paper_2309_08079_gb300 import _lib
-    assert ctypes.sizeof(_lib.mpcg_stats) == 24
-    assert ctypes.sizeof(_lib.mpcg_opts) == 40
-    assert ctypes.sizeof(_lib.mpcg_dims) == 16
-    assert ctypes.sizeof(_lib.mpcg_schur) == 6 * ctypes.sizeof(ctypes.c_void_p)
+    structs = {n: getattr(_lib, n) for n in ("mpcg_dims", "mpcg_lq", "mpcg_schur", "mpcg_opts",
+                                             "mpcg_stats", "mpcg_grads", "mpcg_model", "mpcg_lq_out")}
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(ROOT, "include")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mpcg.h"', "int main(void) {"]
+    for n, st in structs.items():
+        lines.append(f'printf("{n} size %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for n, st in structs.items():
+        assert got[(n, "size")] == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert got[(n, f)] == getattr(st, f).offset, (n, f)
 
 
 def test_workspace_bytes_is_host_only(lib_path):

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import TOL_F32, solver
+from gpu_util import TOL_F32, TOL_KNOT_F32, knot_err, solver
 from workload import gen
 
 pytestmark = pytest.mark.gpu
@@ -37,6 +37,8 @@ def _check_lam(batch, lam, st, los, which=None):
         assert st["status"][b] == 0, (b, st[b])
         e = oracle.relerr(lam[ko[b]:ko[b + 1]], los[b])
         assert e < TOL_F32, (b, batch.items[b].N, e)
+        ek = knot_err(lam[ko[b]:ko[b + 1]], los[b])
+        assert ek < TOL_KNOT_F32, (b, batch.items[b].N, ek)
 
 
 @pytest.mark.parametrize("mode", [1, 2, 3])

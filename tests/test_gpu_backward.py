@@ -37,15 +37,63 @@ def _oracle_grads(lq64, w):
     return oracle.grad(lq64, lam, dx, du, w, 2 * dx, 2 * du)
 
 
+# float32 gradient against the oracle's analytic gradient, field by field
+# (normwise): about 3x the largest error measured on these shapes.
+GRAD_BAR_F32 = 2.5e-4
+
+
 @pytest.mark.parametrize("N", [2, 16, 128])
 def test_backward_vs_oracle_f32(N):
     lq = gen.kuka_lq(14, 7, N, 4000 + N).astype(np.float32)
     w = gen.loss_weights(N * 14, 4).reshape(N, 14)
     g, _ = _gpu_grads(lq, w)
     go = _oracle_grads(lq.astype(np.float64), w)
-    for f in FIELDS:
-        e = oracle.relerr(g[f], go[f])
-        assert e < 1e-3, (f, e)
+    errs = {f: oracle.relerr(g[f], go[f]) for f in FIELDS}
+    print(f"N={N}", errs)
+    assert max(errs.values()) < GRAD_BAR_F32, errs
+
+
+def test_gradient_config_central_differences():
+    """The gradient workload's check: one instance of the 64 x N = 128 batch
+    (seed 4000), loss sum ||dz||^2 + w^T lambda with w from seed 4; the float32
+    GPU gradient at 50 coordinates of (A, B, Qd, Rd, q, r, c), drawn with
+    seed 4 uniformly over the concatenated parameters, against FP64 central
+    differences (h = 1e-6) of the oracle's loss."""
+    c = gen.CONFIG_GRAD
+    N, nx = c["N"], c["nx"]
+    lq = gen.kuka_lq(nx, c["nu"], N, c["seed_base"], dt=c["dt"], qd=c["qd"]).astype(np.float32)
+    w = gen.loss_weights(c["B"] * N * nx, c["w_seed"])[:N * nx].reshape(N, nx)
+    g, _ = _gpu_grads(lq, w)
+    lq64 = lq.astype(np.float64)
+
+    def L(l):
+        lam, dx, du = oracle.kkt_solve(l)
+        return oracle.loss(lam, dx, du, w)
+
+    h = c["fd_h"]
+    L0 = L(lq64)
+    round_err = 50 * np.finfo(np.float64).eps * abs(L0) / h
+    sizes = [getattr(lq64, f).size for f in FIELDS]
+    rng = np.random.default_rng(c["w_seed"])
+    flat = rng.choice(sum(sizes), size=c["fd_coords"], replace=False)
+    offs = np.cumsum([0] + sizes)
+    worst = 0.0
+    for j in flat:
+        fi = int(np.searchsorted(offs, j, side="right") - 1)
+        f = FIELDS[fi]
+        idx = np.unravel_index(int(j - offs[fi]), getattr(lq64, f).shape)
+        p, m = lq64.copy(), lq64.copy()
+        getattr(p, f)[idx] += h
+        getattr(m, f)[idx] -= h
+        fd = (L(p) - L(m)) / (2 * h)
+        # relative to the coordinate, with a floor at 1e-2 of the field's
+        # largest gradient entry (a coordinate whose derivative nearly
+        # cancels is held to the field's scale)
+        scale = max(abs(fd), 1e-2 * np.abs(g[f]).max())
+        err = (abs(g[f][idx] - fd) - round_err) / scale
+        worst = max(worst, err)
+        assert err < 1e-3, (f, idx, g[f][idx], fd, err)
+    print(f"worst scaled error over {len(flat)} coordinates: {worst:.2e}")
 
 
 def test_backward_f64_vs_oracle_and_central_differences():
@@ -90,4 +138,4 @@ def test_backward_batched():
             else:
                 sl = slice(ko[b], ko[b + 1])
             e = oracle.relerr(g[f][sl], go[f])
-            assert e < 1e-3, (b, f, e)
+            assert e < GRAD_BAR_F32, (b, f, e)

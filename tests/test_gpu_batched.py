@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import TOL_F32, TOL_F64, solver
+from gpu_util import TOL_F32, TOL_F64, TOL_KNOT_F32, TOL_KNOT_F64, assert_knots, solver
 from workload import gen
 
 pytestmark = pytest.mark.gpu
@@ -32,6 +32,8 @@ def _check(batch, lam, dx, du, st, tol):
         z = np.concatenate([dx[ko[b]:ko[b + 1]].ravel(), du[co[b]:co[b + 1]].ravel()])
         e_dz = oracle.relerr(z, np.concatenate([xo.ravel(), uo.ravel()]))
         assert e_lam < tol and e_dz < tol, (b, it.N, e_lam, e_dz)
+        assert_knots(lam[ko[b]:ko[b + 1]], dx[ko[b]:ko[b + 1]], du[co[b]:co[b + 1]], lo, xo, uo,
+                     TOL_KNOT_F32 if tol >= TOL_F32 else TOL_KNOT_F64, (b, it.N))
 
 
 @pytest.mark.parametrize("mode", [1, 2, 3, 4])

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import TOL_F32, TOL_F64, parity, run_gpu, solver
+from gpu_util import TOL_F32, TOL_F64, TOL_KNOT_F32, assert_knots, parity, run_gpu, solver
 from workload import gen
 
 pytestmark = pytest.mark.gpu
@@ -68,6 +68,8 @@ def test_dense_cost_batched(mode):
         assert oracle.relerr(lam[ko[b]:ko[b + 1]], lo) < TOL_F32
         z = np.concatenate([dx[ko[b]:ko[b + 1]].ravel(), du[co[b]:co[b + 1]].ravel()])
         assert oracle.relerr(z, np.concatenate([xo.ravel(), uo.ravel()])) < TOL_F32
+        assert_knots(lam[ko[b]:ko[b + 1]], dx[ko[b]:ko[b + 1]], du[co[b]:co[b + 1]], lo, xo, uo,
+                     TOL_KNOT_F32, b)
 
 
 def test_dense_block_not_spd_is_bad_input():

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import TOL_F32, oracle_solution, solver
+from gpu_util import TOL_F32, TOL_KNOT_F32, assert_knots, oracle_solution, solver
 from workload import gen
 
 pytestmark = pytest.mark.gpu
@@ -32,6 +32,8 @@ def _check_sample(batch, lam, dx, du, st, picks, tol_lam, tol_dz):
         z = np.concatenate([dx[ko[b]:ko[b + 1]].ravel(), du[co[b]:co[b + 1]].ravel()])
         e_dz = oracle.relerr(z, np.concatenate([xo.ravel(), uo.ravel()]))
         assert e_lam < tol_lam and e_dz < tol_dz, (b, batch.Ns[b], e_lam, e_dz)
+        assert_knots(lam[ko[b]:ko[b + 1]], dx[ko[b]:ko[b + 1]], du[co[b]:co[b + 1]], lo, xo, uo,
+                     TOL_KNOT_F32, (b, batch.Ns[b]))
 
 
 def test_sweep_warm_started_every_horizon():
@@ -52,11 +54,12 @@ def test_sweep_warm_started_every_horizon():
                                    device="cuda")
             lam, dx, du, st, _ = s.solve(lt, lam0, opts=make_opts(), schur=sch)
             torch.cuda.synchronize()
-            e_lam = oracle.relerr(lam.cpu().double().numpy(), lo)
-            e_dz = oracle.relerr(np.concatenate([dx.cpu().double().numpy().ravel(),
-                                                 du.cpu().double().numpy().ravel()]),
+            lam_, dx_, du_ = (t.cpu().double().numpy() for t in (lam, dx, du))
+            e_lam = oracle.relerr(lam_, lo)
+            e_dz = oracle.relerr(np.concatenate([dx_.ravel(), du_.ravel()]),
                                  np.concatenate([xo.ravel(), uo.ravel()]))
             assert e_lam < TOL_F32 and e_dz < TOL_F32, (N, rep, e_lam, e_dz)
+            assert_knots(lam_, dx_, du_, lo, xo, uo, TOL_KNOT_F32, (N, rep))
 
 
 def test_batch256_full_size():
@@ -109,8 +112,7 @@ def test_large_state_batch_full_size():
     batch = gen.kuka_batch(c["nx"], c["nu"], Ns, c["seed_base"], dt=c["dt"], qd=c["qd"]).astype(np.float32)
     picks = [int(np.argmin(Ns)), int(np.argmax(Ns)), 19] + list(range(0, batch.B, 211))
     # each refinement step contracts the error by about the plain float32
-    # error of the instance (up to ~3e-3 here): one step meets the parity
-    # bar, two go below 1e-6
+    # error of the instance: one step meets the parity bar, two go below 1e-6
     lam, dx, du, st = _solve_batch(batch, refine=1)
     _check_sample(batch, lam, dx, du, st, picks, TOL_F32, TOL_F32)
     lam, dx, du, st = _solve_batch(batch, refine=2)
@@ -146,4 +148,5 @@ def test_gradient_batch_full_size():
         go = oracle.grad(it, lo, xo, uo, w[ko[b]:ko[b + 1]], 2 * xo, 2 * uo)
         for f in fields:
             sl = slice(co[b], co[b + 1]) if f in ("A", "B", "Rd", "r") else slice(ko[b], ko[b + 1])
-            assert oracle.relerr(g[f][sl], go[f]) < 1e-3, (b, f)
+            e = oracle.relerr(g[f][sl], go[f])
+            assert e < 2.5e-4, (b, f, e)
