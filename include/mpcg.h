@@ -414,6 +414,25 @@ int mpcg_line_search_batched(mpcg_handle *h, mpcg_dims dims, int B, const int *k
  * run out by construction; the context stays usable. */
 int mpcg_selftest_wait(mpcg_handle *h, int push, double limit_s, int *status, void *stream);
 
+/* Diagnostic of the give-up path (not in the paper).  A cluster CTA whose
+ * bounded wait gave up must not leave while peers may still push into its
+ * shared memory, nor leave its peers waiting out their own limits: the PCG
+ * kernels then drain the cluster -- set an abort flag in every peer (their
+ * waits poll it), arrive once on every peer's "stopped" mbarrier, wait
+ * (bounded) for every peer's arrival, let pushes in flight land, leave.
+ * This call runs that path in one four-CTA cluster where every CTA expects a
+ * 4-byte push from each of the other three.  mode 0: every CTA pushes and
+ * every wait completes.  mode 1: CTA 0 withholds its pushes and gives up at
+ * once; the other three cannot complete and are released by the abort flag.
+ * Waits are bounded by limit_s seconds (1e-3 <= limit_s <= 1, else
+ * MPCG_EINVAL).  DEVICE outputs, one entry per CTA: status[4] =
+ * MPCG_CONVERGED (wait completed), MPCG_TIMEOUT (gave up or was told to
+ * stop, and every peer reported stopping) or -MPCG_TIMEOUT (a peer never
+ * reported within the limit); elapsed_ns[4] = nanoseconds from the start of
+ * its wait to its exit (well below limit_s when the flag released it). */
+int mpcg_selftest_drain(mpcg_handle *h, int mode, double limit_s, int *status,
+                        unsigned long long *elapsed_ns, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,7 @@ EXPORTS = (
     "mpcg_backward_batched_noalloc", "mpcg_refine_step", "mpcg_refine_step_batched",
     "mpcg_linearize", "mpcg_linearize_batched", "mpcg_line_search", "mpcg_line_search_batched",
     "mpcg_form_schur_precon", "mpcg_form_schur_precon_batched", "mpcg_selftest_wait",
+    "mpcg_selftest_drain",
 )
 
 
@@ -152,6 +153,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                              vp, vp, vp, C.c_double, i32, vp, vp, vp]
     lib.mpcg_selftest_wait.restype = i32
     lib.mpcg_selftest_wait.argtypes = [vp, i32, C.c_double, vp, vp]
+    lib.mpcg_selftest_drain.restype = i32
+    lib.mpcg_selftest_drain.argtypes = [vp, i32, C.c_double, vp, vp, vp]
     _lib = lib
     return lib
 

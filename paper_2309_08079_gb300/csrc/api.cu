@@ -329,7 +329,9 @@ int backward_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, c
         rc = err_cuda(launch_resid<T>(d.nx, d.nu, bv, Kgrid, A, Bm, Qd, Rd, nullptr, nullptr, lbar,
                                       T(-1), mu, res, st));
         if (rc) return rc;
-        rc = err_cuda(cudaMemsetAsync(delta, 0, (size_t)Kgrid * d.nx * sizeof(T), st));
+        // delta is the caller's [K][nx] array: zero the batch's own K knots
+        // (a memset of the launch's Kgrid = B * N knots would overrun it)
+        rc = err_cuda(launch_zero<T>(d.nx, bv, Kgrid, delta, st));
         if (rc) return rc;
         rc = pcg_t<T>(h, d, B, knot_off, s, res, T(1), delta, o, nullptr, ws, st);
         if (rc) return rc;

@@ -181,6 +181,16 @@ __device__ __forceinline__ void cluster_sync_all() {
                  "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// Named CTA barrier `id` (1..15) over `n` threads: producers arrive without
+// waiting, the consumer waits for all n; the producers' earlier shared-memory
+// stores are visible to the consumer after its bar.sync.
+__device__ __forceinline__ void named_bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -271,6 +281,61 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
         if (mbar_try_wait(mbar, parity)) return true;
         if (global_ns() - t0 > limit_ns) return false;
     }
+}
+
+// As mbar_wait_bounded, and also gives up once the word at shared address
+// `abort_flag` (this CTA's shared memory) is non-zero: a peer that has given
+// up sets it.  The flag is read only after the fast spin, so a healthy
+// exchange never pays for it.
+__device__ __forceinline__ bool mbar_wait_bounded_abort(uint32_t mbar, uint32_t parity, uint64_t limit_ns,
+                                                        const volatile int *abort_flag) {
+    for (int i = 0; i < 4096; ++i)
+        if (mbar_test_wait(mbar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// One arrival on the mbarrier at shared::cluster address `mbar` (a peer's),
+// ordered after this thread's earlier memory operations (release, cluster).
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_cluster() {
+    asm volatile("fence.acq_rel.cluster;" ::: "memory");
+}
+
+// Bounded busy wait of about `ns` nanoseconds.
+__device__ __forceinline__ void spin_ns(uint64_t ns) {
+    const uint64_t t0 = global_ns();
+    while (global_ns() - t0 < ns) {
+    }
+}
+
+// Leaving a cluster after a wait gave up (called by one thread of the CTA).
+// A CTA must not leave while peers may still push into its shared memory:
+// it tells every peer to stop (their bounded waits poll `abort_flag`),
+// reports to every peer that it has stopped pushing (one arrival on each
+// peer's `stopped` mbarrier, initialised with C - 1 arrivals), waits up to
+// `limit_ns` until every peer has reported the same, and lets pushes
+// already in flight land (`grace_ns`).  Best effort: a peer that is stuck
+// for good never reports, and the wait gives up.  Returns true if every
+// peer reported.
+__device__ __forceinline__ bool cluster_drain(uint32_t rank, uint32_t C, uint32_t abort_flag, uint32_t stopped,
+                                              uint64_t limit_ns, uint64_t grace_ns) {
+    if (C < 2) return true;
+    for (uint32_t q = 0; q < C; ++q)
+        if (q != rank) st_cluster(map_rank(abort_flag, q), 1);
+    fence_acq_rel_cluster();
+    for (uint32_t q = 0; q < C; ++q)
+        if (q != rank) mbar_arrive_remote(map_rank(stopped, q));
+    const bool all = mbar_wait_bounded(stopped, 0u, limit_ns);
+    spin_ns(grace_ns);
+    return all;
 }
 
 __device__ __forceinline__ void st_async(uint32_t addr, float v, uint32_t mbar) {

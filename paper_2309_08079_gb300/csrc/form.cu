@@ -424,6 +424,15 @@ __global__ void axpy_kernel(int nx, BatchView bv, const T *__restrict__ d, T *__
         lam[i] += d[i];
 }
 
+// v[i] = 0 over every knot of the batch (a caller's [K][nx] array, K = the
+// batch's own knot count, which only the device knows for a ragged batch)
+template <typename T>
+__global__ void zero_kernel(int nx, BatchView bv, T *__restrict__ v) {
+    const size_t n = (size_t)bv.total() * nx;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        v[i] = T(0);
+}
+
 // ---------------------------------------------------------------------------
 // Fused formation (diagonal costs): block row k of S+ and gamma_k (Sec.
 // II-B, Eq. schur and Eq. trajoptSchur_1/2, as form_schur_kernel), Pd[k] =
@@ -988,6 +997,14 @@ cudaError_t launch_axpy(int nx, BatchView bv, int Kgrid, const T *d, T *lam, cud
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_zero(int nx, BatchView bv, int Kgrid, T *v, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = std::max(1, std::min(1024, ceil_div(Kgrid * nx, threads)));
+    zero_kernel<T><<<blocks, threads, 0, s>>>(nx, bv, v);
+    return cudaGetLastError();
+}
+
 // Raise every per-knot kernel's dynamic shared-memory ceiling once per device
 // (large nx needs more than the 48 KB default).
 template <typename T>
@@ -1028,6 +1045,7 @@ cudaError_t form_prepare(int smem_optin) {
                                          const T *, const T *, const T *, const T *, const T *,   \
                                          T, const T *, T *, cudaStream_t);                        \
     template cudaError_t launch_axpy<T>(int, BatchView, int, const T *, T *, cudaStream_t);     \
+    template cudaError_t launch_zero<T>(int, BatchView, int, T *, cudaStream_t);                 \
     template cudaError_t launch_form_fused<T>(const SchurArgs<T> &, T *, T *, int, cudaStream_t); \
     template size_t form_fused_smem_bytes<T>(int, int, int, int);                                \
     template cudaError_t launch_recover_dense<T>(int, int, BatchView, int, const T *, const T *, \

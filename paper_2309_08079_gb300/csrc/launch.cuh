@@ -82,6 +82,8 @@ cudaError_t launch_resid(int nx, int nu, BatchView bv, int Kgrid, const T *A, co
                          T *out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_axpy(int nx, BatchView bv, int Kgrid, const T *d, T *lam, cudaStream_t s);
+template <typename T>
+cudaError_t launch_zero(int nx, BatchView bv, int Kgrid, T *v, cudaStream_t s);
 template <typename T> cudaError_t pcg_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
 template <typename T> int pcg_max_clusters(const PcgLaunch &);
 cudaError_t pcg_prepare(int smem_optin);

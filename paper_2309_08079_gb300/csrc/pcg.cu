@@ -19,17 +19,23 @@
 //    thread's rows of lambda, r, p stay in registers.
 //
 // Communication: two exchanges per iteration, one per reduction of
-// Algorithm 1 (A: p^T S p; B: r^T r~ and ||r||^2).  Each CTA reduces its
-// partial sum, then pushes it with st.async into every CTA of the cluster
-// (its own included); the pushes complete transaction bytes on the
-// receiver's mbarrier, so a CTA waits only for the data it needs and no
-// cluster-wide barrier or fence sits on the critical path.  The same
-// exchanges carry the halo rows the next phase needs (S p of the boundary
-// knots with A, Phi^-1 r with B), so Algorithm 2's separate neighbour loads
-// of p and r cost nothing extra: a CTA updates its halo copies of r and p
-// with the same fused multiply-adds the owner uses (bit-identical).
-// Every CTA adds the C partials in rank order, so all CTAs take identical
-// scalar decisions (alpha, beta, exit).
+// Algorithm 1 (A: p^T S p; B: r^T r~ and ||r||^2).  Each warp reduces its
+// lanes; the warps hand their partials to warp 0 through shared memory (a
+// named barrier that only warp 0 waits on), and warp 0 pushes the CTA's
+// partial with st.async into every CTA of the cluster (its own included).
+// The pushes complete transaction bytes on the receiver's mbarrier, so a
+// CTA waits only for the data it needs and no cluster-wide barrier or fence
+// sits on the critical path.  One push per source CTA matters: a receiver
+// takes in the pushes of an exchange one after another (measured on GB300:
+// ~6.6 cycles each), and one push per warp (C*W = 128 at N = 512) made the
+// exchange ~1.5x longer.  The same exchanges carry the halo rows the next
+// phase needs (S p of the boundary knots with A, Phi^-1 r with B; in REG
+// mode four 16-byte pushes per side), so Algorithm 2's separate neighbour
+// loads of p and r cost nothing extra: a CTA updates its halo copies of r
+// and p with the same fused multiply-adds the owner uses (bit-identical).
+// Every CTA adds the C partials in the same butterfly order (the pair
+// additions are commutative), so all CTAs take identical scalar decisions
+// (alpha, beta, exit).
 //
 // Dot products: exact float products accumulated as float pairs (see
 // common.cuh), or in float64 (mpcg_opts.dot = 1, the AccF64 policy); ||r||^2,
@@ -42,6 +48,7 @@
 namespace mpcg {
 
 constexpr int CMAX = 16;
+constexpr int WMAX = 16;  // warps per CTA (512 threads)
 
 template <typename A>
 struct PayB;  // payload of exchange B: (r^T r~, ||r||^2), by accumulator type
@@ -65,7 +72,7 @@ __device__ __forceinline__ double rr_acc(double r, double acc) { return __fma_rn
 // on the host (pcg_smem_bytes) and the device.  A: accumulator type.
 template <typename T, typename A>
 struct SmemLayout {
-    size_t vecP, vecR, haloA, haloB, slotA, slotB, mbar, misc, mats, total;
+    size_t vecP, vecR, haloA, haloB, slotA, slotB, wpartA, wpartB, mbar, misc, mats, total;
     __host__ __device__ SmemLayout(int kpc_max, int vs, int W, int nx, int stage) {
         size_t o = 0;
         auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
@@ -73,9 +80,12 @@ struct SmemLayout {
         vecR = o; o = al(o + sizeof(T) * (kpc_max + 2) * vs);
         haloA = o; o = al(o + sizeof(T) * 2 * vs);
         haloB = o; o = al(o + sizeof(T) * 2 * vs);
-        slotA = o; o = al(o + sizeof(A) * CMAX * W);
-        slotB = o; o = al(o + sizeof(PayB<A>) * CMAX * W);
-        mbar = o; o = al(o + 2 * sizeof(uint64_t));
+        slotA = o; o = al(o + sizeof(A) * CMAX);
+        slotB = o; o = al(o + sizeof(PayB<A>) * CMAX);
+        wpartA = o; o = al(o + sizeof(A) * WMAX);
+        wpartB = o; o = al(o + sizeof(PayB<A>) * WMAX);
+        (void)W;
+        mbar = o; o = al(o + 3 * sizeof(uint64_t));  // exchange A, exchange B, peers stopped
         misc = o; o = al(o + 16);
         mats = o;
         if (stage) o = al(o + sizeof(T) * (size_t)(4 * kpc_max + 2) * nx * nx);
@@ -204,8 +214,11 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
     T *haloB = reinterpret_cast<T *>(smem + L.haloB);
     A *slotA = reinterpret_cast<A *>(smem + L.slotA);
     PB *slotB = reinterpret_cast<PB *>(smem + L.slotB);
+    A *wpartA = reinterpret_cast<A *>(smem + L.wpartA);
+    PB *wpartB = reinterpret_cast<PB *>(smem + L.wpartB);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + L.mbar);
     int *s_inst = reinterpret_cast<int *>(smem + L.misc);
+    int *s_abort = s_inst + 1;  // set by a peer that gave up waiting
     T *mats = reinterpret_cast<T *>(smem + L.mats);
 
     const bool has_left = rank > 0, has_right = rank + 1 < C;
@@ -216,18 +229,27 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
     const uint32_t mbB_l = map_rank(mbB, rl), mbB_r = map_rank(mbB, rr_);
     const uint32_t hA_l = map_rank(smem_u32(haloA + vs), rl), hA_r = map_rank(smem_u32(haloA), rr_);
     const uint32_t hB_l = map_rank(smem_u32(haloB + vs), rl), hB_r = map_rank(smem_u32(haloB), rr_);
-    // lane q < C of every warp pushes the warp's partial to slot [rank][warp] of CTA q
+    // lane q < C of warp 0 pushes the CTA's partial to slot [rank] of CTA q
     const uint32_t peer = lane < C ? lane : 0;
-    const uint32_t slotA_peer = map_rank(smem_u32(slotA + rank * W + warp), peer);
-    const uint32_t slotB_peer = map_rank(smem_u32(slotB + rank * W + warp), peer);
+    const uint32_t slotA_peer = map_rank(smem_u32(slotA + rank), peer);
+    const uint32_t slotB_peer = map_rank(smem_u32(slotB + rank), peer);
     const uint32_t mbA_peer = map_rank(mbA, peer), mbB_peer = map_rank(mbB, peer);
-    const uint32_t bytesA_slots = C * W * (uint32_t)sizeof(A), bytesB_slots = C * W * (uint32_t)sizeof(PB);
-    const int nslots = (int)C * W;
-    const uint32_t halo_bytes = (uint32_t)(nx * sizeof(T)) * ((has_left ? 1u : 0u) + (has_right ? 1u : 0u));
+    const uint32_t bytesA_slots = C * (uint32_t)sizeof(A), bytesB_slots = C * (uint32_t)sizeof(PB);
+    // butterfly widths: warps per CTA and CTAs per cluster, rounded up to powers of two (<= 16)
+    int wpow = 1, cpow = 1;
+    while (wpow < W) wpow <<= 1;
+    while (cpow < (int)C) cpow <<= 1;
+    // REG mode sends a boundary knot's 16-float slot (14 rows and 2 zeros) as
+    // four 16-byte pushes; PTR mode one push per row
+    const uint32_t side_bytes = MODE == MODE_REG ? 16u * (uint32_t)sizeof(float) : (uint32_t)(nx * sizeof(T));
+    const uint32_t halo_bytes = side_bytes * ((has_left ? 1u : 0u) + (has_right ? 1u : 0u));
 
+    const uint32_t mbS = smem_u32(&mbar[2]);  // one arrival per peer that has stopped pushing
     if (tid == 0) {
         mbar_init(mbA, 1);
         mbar_init(mbB, 1);
+        mbar_init(mbS, C > 1 ? C - 1 : 1);
+        *s_abort = 0;
         fence_mbar_init();
     }
     cluster_sync_all();  // peers may push only after every mbarrier is initialised
@@ -369,54 +391,97 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
             }
         };
 
+        // the warps holding the first and last knot slot (warp-uniform)
+        const bool warp_left = has_left && warp == 0;
+        const bool warp_right = has_right && (int)warp == ((KPC - 1) * LPK) / 32;
         // Push this knot's boundary rows into the neighbours' halo slots.
         auto push_halo = [&](uint32_t h_l, uint32_t m_l, uint32_t h_r, uint32_t m_r, const T (&val)[RPT]) {
+            if constexpr (MODE == MODE_REG) {
+                // Rows 4j..4j+3 gathered into lane j (< 4) of the knot's group:
+                // row i sits in lane i % 8 as val[i / 8]; rows 14, 15 are zero.
+                if (!(warp_left || warp_right)) return;
+                const int base = (int)lane & ~(LPK - 1), j = (int)lane & (LPK - 1);
+                const int src0 = base + (j & 1) * 4;
+                float x[4];
 #pragma unroll
-            for (int m = 0; m < RPT; ++m) {
-                if (!rx[m]) continue;
-                const uint32_t off = rows[m] * (uint32_t)sizeof(T);
-                if (send_left) st_async(h_l + off, val[m], m_l);
-                if (send_right) st_async(h_r + off, val[m], m_r);
+                for (int t = 0; t < 4; ++t) {
+                    const float a = __shfl_sync(0xffffffffu, val[0], src0 + t);
+                    const float b = __shfl_sync(0xffffffffu, val[1], src0 + t);
+                    x[t] = (j & 2) ? b : a;
+                }
+                if (j < 4) {
+                    const uint32_t off = 16u * (uint32_t)j;
+                    if (send_left) st_async_v4(h_l + off, x[0], x[1], x[2], x[3], m_l);
+                    if (send_right) st_async_v4(h_r + off, x[0], x[1], x[2], x[3], m_r);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < RPT; ++m) {
+                    if (!rx[m]) continue;
+                    const uint32_t off = rows[m] * (uint32_t)sizeof(T);
+                    if (send_left) st_async(h_l + off, val[m], m_l);
+                    if (send_right) st_async(h_r + off, val[m], m_r);
+                }
             }
         };
 
         // Exchange A: cluster sum of one accumulator per thread.  Each warp
-        // reduces its lanes and pushes the warp partial into slot
-        // [rank][warp] of every CTA; after the wait every warp adds the C*W
-        // slots in one fixed order (lane-strided, then a shuffle tree).
+        // reduces its lanes; lane 0 stores the warp partial, the other warps
+        // arrive on named barrier 1 and go on to the exchange's CTA barrier,
+        // warp 0 waits there, adds the W partials and its lanes q < C push
+        // the CTA partial into slot [rank] of CTA q.  After the wait every
+        // warp adds the C slots (butterfly over lanes mod cpow).
         auto exchangeA = [&](A v) -> A {
 #pragma unroll
             for (int m = 16; m >= 1; m >>= 1) v = AT::add_tree(v, AT::shfl_xor(v, m));
-            if (lane < C) st_async_pay(slotA_peer, v, mbA_peer);
+            if (lane == 0) wpartA[warp] = v;
+            if (warp == 0) {
+                named_bar_sync(1, nthreads);
+                // every group of wpow lanes loads the W partials, so every
+                // lane (in particular lanes q < C) ends with the CTA total
+                const int wq = (int)lane & (wpow - 1);
+                A y = wq < W ? wpartA[wq] : AT::zero();
+                for (int m = wpow >> 1; m >= 1; m >>= 1) y = AT::add_tree(y, AT::shfl_xor(y, m));
+                if (lane < C) st_async_pay(slotA_peer, y, mbA_peer);
+            } else {
+                named_bar_arrive(1, nthreads);
+            }
             int fail = 0;
             if (tid == 0) {
                 mbar_arrive_expect(mbA, bytesA_slots + halo_bytes);
-                fail = !mbar_wait_bounded(mbA, phA, WAIT_LIMIT_NS);
+                fail = !mbar_wait_bounded_abort(mbA, phA, WAIT_LIMIT_NS, s_abort);
             }
             phA ^= 1u;
             if (__syncthreads_or(fail)) timed_out = true;
-            A t = AT::zero();
-            for (int q = lane; q < nslots; q += 32) t = AT::add_tree(t, slotA[q]);
-#pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) t = AT::add_tree(t, AT::shfl_xor(t, m));
+            const int q = (int)lane & (cpow - 1);
+            A t = q < (int)C ? slotA[q] : AT::zero();
+            for (int m = cpow >> 1; m >= 1; m >>= 1) t = AT::add_tree(t, AT::shfl_xor(t, m));
             return t;
         };
         // Exchange B: cluster sums of (r^T r~, ||r||^2), same pattern.
         auto exchangeB = [&](PB v) -> PB {
 #pragma unroll
             for (int m = 16; m >= 1; m >>= 1) v = payb_add<A>(v, payb_shfl<A>(v, m));
-            if (lane < C) st_async_pay(slotB_peer, v, mbB_peer);
+            if (lane == 0) wpartB[warp] = v;
+            if (warp == 0) {
+                named_bar_sync(1, nthreads);
+                const int wq = (int)lane & (wpow - 1);
+                PB y = wq < W ? wpartB[wq] : payb_zero<A>();
+                for (int m = wpow >> 1; m >= 1; m >>= 1) y = payb_add<A>(y, payb_shfl<A>(y, m));
+                if (lane < C) st_async_pay(slotB_peer, y, mbB_peer);
+            } else {
+                named_bar_arrive(1, nthreads);
+            }
             int fail = 0;
             if (tid == 0) {
                 mbar_arrive_expect(mbB, bytesB_slots + halo_bytes);
-                fail = !mbar_wait_bounded(mbB, phB, WAIT_LIMIT_NS);
+                fail = !mbar_wait_bounded_abort(mbB, phB, WAIT_LIMIT_NS, s_abort);
             }
             phB ^= 1u;
             if (__syncthreads_or(fail)) timed_out = true;
-            PB t = payb_zero<A>();
-            for (int q = lane; q < nslots; q += 32) t = payb_add<A>(t, slotB[q]);
-#pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) t = payb_add<A>(t, payb_shfl<A>(t, m));
+            const int q = (int)lane & (cpow - 1);
+            PB t = q < (int)C ? slotB[q] : payb_zero<A>();
+            for (int m = cpow >> 1; m >= 1; m >>= 1) t = payb_add<A>(t, payb_shfl<A>(t, m));
             return t;
         };
 
@@ -618,9 +683,15 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
             st.relres = bbd > 0.0 ? sqrt(rrd / bbd) : sqrt(rrd);
             P.stats[b] = st;
         }
-        // a CTA whose wait gave up leaves at once: it must not enter another
-        // cluster-wide barrier that a stuck peer would never reach
-        if (timed_out) return;
+        // A CTA whose wait gave up (or that a peer told to stop) must not
+        // enter another cluster-wide barrier, which a stuck peer would never
+        // reach, nor leave while peers may still push into its shared
+        // memory: it drains the cluster (cluster_drain) and leaves.
+        if (timed_out) {
+            if (tid == 0) cluster_drain(rank, C, smem_u32(s_abort), mbS, DRAIN_LIMIT_NS, DRAIN_GRACE_NS);
+            __syncthreads();
+            return;
+        }
         // every CTA is done with this instance's shared data before the next
         // instance id is pushed
         cluster_sync_all();

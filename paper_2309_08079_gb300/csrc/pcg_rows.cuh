@@ -7,6 +7,8 @@
 namespace mpcg {
 
 constexpr uint64_t WAIT_LIMIT_NS = 4000000000ull;  // 4 s: never reached in a healthy run
+constexpr uint64_t DRAIN_LIMIT_NS = 100000000ull;  // 0.1 s for the peers to stop after a give-up
+constexpr uint64_t DRAIN_GRACE_NS = 20000ull;      // pushes already in flight land within this
 
 // Row i of one block row times the halo'd vector (PTR mode).  D: diagonal
 // block (symmetric: column i == row i); L: block (k, k-1) read by rows;

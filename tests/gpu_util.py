@@ -10,12 +10,16 @@ from workload import gen
 TOL_F32 = 1e-4
 TOL_F64 = 1e-9
 # Per knot: max over k of ||x_k - x*_k|| / ||x*_k|| for lambda_k, dx_k and
-# du_k separately.  The FP32 floor is the rounding of S+ to float32: the
-# exact solve of the rounded S+ is already up to 9.4e-5 (lambda_k),
-# 1.2e-4 (dx_k) and 2.6e-4 (du_k) from the oracle per knot at N = 512,
-# seed 514.  A wrong row of one knot (a halo copy, a CTA boundary) shows up
-# here long before it moves the normwise error.
+# du_k separately.  lambda_k is the PCG's own output: the exact solve of S+
+# rounded to float32 is up to 9.4e-5 from the oracle per knot at N = 512,
+# seed 514, and a wrong row of one knot (a halo copy, a CTA boundary) shows
+# up here long before it moves the normwise error.  dz is recovered per knot
+# from lambda through dx_k = (lambda_k - A_k^T lambda_{k+1} - q_k) / Qd_k,
+# which cancels where A_k ~ I: storing even the exact lambda in float32
+# leaves up to 7e-4 in dx_k at the worst knot (nx = 36, dt = 0.005), so
+# dx_k and du_k have their own bar.
 TOL_KNOT_F32 = 1e-3
+TOL_KNOT_DZ_F32 = 5e-3
 TOL_KNOT_F64 = 1e-8
 
 
@@ -55,8 +59,11 @@ def knot_errs(lam, dx, du, lo, xo, uo):
 
 
 def assert_knots(lam, dx, du, lo, xo, uo, bar=TOL_KNOT_F32, what=""):
+    """Per-knot bars: `bar` on lambda_k; on dx_k and du_k the float32 dz bar
+    (5x) when `bar` is the float32 lambda bar, else `bar` itself."""
     e = knot_errs(lam, dx, du, lo, xo, uo)
-    assert max(e) < bar, ("per-knot error (lambda, dx, du)", what, e)
+    bar_dz = TOL_KNOT_DZ_F32 if bar == TOL_KNOT_F32 else bar
+    assert e[0] < bar and max(e[1:]) < bar_dz, ("per-knot error (lambda, dx, du)", what, e)
     return e
 
 

@@ -428,6 +428,40 @@ def test_bounded_wait_runs_out_and_reports_timeout():
     assert stt["status"][0] == 0 and e_lam < TOL_F32 and e_dz < TOL_F32
 
 
+def test_give_up_drains_the_cluster():
+    """The PCG kernels' give-up path in a four-CTA cluster: with every push
+    made, all waits complete; when CTA 0 withholds its pushes and gives up at
+    once, its drain's abort flag releases the other three (within a small
+    fraction of their 1 s limit), every CTA reports MPCG_TIMEOUT with every
+    peer having reported stopping, and the context stays usable."""
+    import torch
+    from paper_2309_08079_gb300._lib import MPCG_TIMEOUT, check
+    s = solver()
+    st = torch.full((4,), -1, dtype=torch.int32, device="cuda")
+    el = torch.zeros(4, dtype=torch.int64, device="cuda")
+    check("mpcg_selftest_drain", s.lib.mpcg_selftest_drain(s.h, 0, 0.5, st.data_ptr(), el.data_ptr(), None))
+    torch.cuda.synchronize()
+    assert st.cpu().tolist() == [0, 0, 0, 0]
+    st.fill_(-1)
+    check("mpcg_selftest_drain", s.lib.mpcg_selftest_drain(s.h, 1, 1.0, st.data_ptr(), el.data_ptr(), None))
+    torch.cuda.synchronize()
+    assert st.cpu().tolist() == [MPCG_TIMEOUT] * 4
+    ns = el.cpu().tolist()
+    assert max(ns[1:]) < 0.1e9, ns  # released by the flag, not by their 1 s limit
+    e_lam, e_dz, stt = parity(gen.kuka_lq(14, 7, 64, 66))
+    assert stt["status"][0] == 0 and e_lam < TOL_F32 and e_dz < TOL_F32
+
+
+def test_drain_selftest_arguments_are_checked():
+    import torch
+    from paper_2309_08079_gb300._lib import MPCG_EINVAL
+    s = solver()
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    el = torch.zeros(4, dtype=torch.int64, device="cuda")
+    for mode, lim in ((2, 0.5), (0, 0.0), (1, 2.0), (0, float("nan"))):
+        assert s.lib.mpcg_selftest_drain(s.h, mode, lim, st.data_ptr(), el.data_ptr(), None) == MPCG_EINVAL
+
+
 def test_bounded_wait_limit_is_checked():
     import torch
     from paper_2309_08079_gb300._lib import MPCG_EINVAL
