@@ -72,6 +72,15 @@ def parse():
     return p.parse_args()
 
 
+def workload_config(world: int = 1) -> dict:
+    """The `config` of both arms' JSON lines (the same workload)."""
+    return {"workload": f"single instance N={NKNOT} nx={NX} nu={NU}, warm-started "
+                        f"(lambda* x (1 + 0.01 xi)), tol 1e-6 relative residual",
+            "seed": SEED, "l2": "flushed between steps (256 MiB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "dot_accumulation": "double-float (f32 pair)"}
+
+
 def workload_lq():
     c = gen.CONFIG_SWEEP
     return gen.kuka_lq(NX, NU, NKNOT, SEED, dt=c["dt"], qd=c["qd"]).astype(np.float32)
@@ -160,6 +169,46 @@ def pcg_bytes_per_knot_iter(nx: int, esize: int = 4) -> int:
     seven vectors."""
     T = nx * (nx + 1) // 2 + nx * nx
     return (2 * T + 7 * nx) * esize
+
+
+def latency_roofline(s, lt, sch, opts, iters_mean: float, launch_us: float, rounds: int = 2000) -> dict:
+    """The single-instance PCG kernel against its synchronisation floor: each
+    iteration of Algorithm 1 takes two cluster reductions, each at least the
+    time mpcg_bench_exchange measures for the launch shape the solve uses
+    (the same exchange code with no arithmetic), so the floor is
+    2 x exchange per iteration.  achieved / peak in PCG iterations per second."""
+    sh = s.pcg_shape(lt, sch, opts)
+    if sh["form"] != "cluster":
+        return {"bound": "n/a", "note": f"kernel form {sh['form']}"}
+    x = s.bench_exchange(sh["C"], sh["threads"] // 32, rounds=rounds)
+    floor_ns = 2.0 * x["ns"]
+    t_it_ns = launch_us * 1e3 / max(iters_mean, 1.0)
+    return {"bound": "sync_latency", "achieved": 1e9 / t_it_ns, "peak": 1e9 / floor_ns,
+            "unit": "PCG iterations/s", "frac": floor_ns / t_it_ns,
+            "peak_source": f"measured: mpcg_bench_exchange on the solve's launch shape "
+                           f"(C={sh['C']} CTAs x {sh['threads'] // 32} warps), 2 exchanges per iteration",
+            "exchange_ns": x["ns"], "exchange_cycles": x["cycles"], "ns_per_iteration": t_it_ns,
+            "floor_ns_per_iteration": floor_ns, "shape": sh}
+
+
+def profile_onchip():
+    """SMEM-pipe share and barrier-stall share of the cluster kernel from the
+    committed ncu summary, when it was taken from the current sources."""
+    prof = os.path.join(ROOT, "profiles", "pcg_cluster_kernel_N512.md")
+    try:
+        txt = open(prof).read()
+        m_sha = re.search(r"cluster kernel sources sha256\[:16\]:\s*([0-9a-f]+)", txt)
+        if not m_sha or m_sha.group(1) != cluster_kernel_sha():
+            return None
+        out = {}
+        for key, pat in (("smem_pipe_frac_active_sms", r"smem_pipe_frac_active_sms:\s*([0-9.eE+-]+)"),
+                         ("barrier_stall_share", r"barrier_stall_share:\s*([0-9.eE+-]+)")):
+            m = re.search(pat, txt)
+            if m:
+                out[key] = float(m.group(1))
+        return out or None
+    except Exception:
+        return None
 
 
 def hbm_peak():
@@ -254,8 +303,7 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": us / 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"single instance N={NKNOT} nx={NX} nu={NU} (latency sweep, largest N)",
-                       "seed": SEED},
+            "config": workload_config(1),
             "cpu_baseline": {"value": us, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": us, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -353,12 +401,19 @@ def run_ours(args, rank, world, local_rank):
     if hbm is None:
         hbm, peak_note = 6800.0, "of fallback"
     achieved = alg_bytes / pcg_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": pcg_traffic_from_profile(),
-                "kernel": "pcg_cluster_kernel", "peak_source": peak_note,
-                "alg_bytes_per_launch": alg_bytes, "launch_us": pcg_s * 1e6}
+    # the kernel's operators stay on chip (registers): what bounds it is the
+    # latency of its two cluster reductions per iteration, measured by the
+    # exchange microbenchmark on the same launch shape; HBM is secondary
+    roofline = latency_roofline(s, lt, sch, opts, float(np.mean(iters)), pcg_s * 1e6)
+    roofline.update({"traffic": pcg_traffic_from_profile(), "kernel": "pcg_cluster_kernel",
+                     "launch_us": pcg_s * 1e6, "onchip_ncu": profile_onchip(),
+                     "hbm": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved / hbm, "peak_source": peak_note,
+                             "alg_bytes_per_launch": alg_bytes}})
 
     batched = backward = sweep = exit_sweep = precon_compare = dense_cost = nmpc = large = None
+    dot64 = run_dot64(s, dev, lq, lam0, flush, min(args.steps, 50), us_default=float(np.mean(pcg_ms)) * 1e3,
+                      iters_default=float(np.mean(iters)))
     if not args.no_sweep:
         sweep = run_sweep(s, dev, args.sweep_reps, flush)
         exit_sweep = run_exit_sweep(s, dev, min(args.sweep_reps, 200))
@@ -391,11 +446,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"single instance N={NKNOT} nx={NX} nu={NU}, warm-started "
-                               f"(lambda* x (1 + 0.01 xi)), tol 1e-6 relative residual",
-                   "seed": SEED, "l2": "flushed between steps (256 MiB write)",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "dot_accumulation": "double-float (f32 pair)"},
+        "config": workload_config(world),
         "step_us": pct(np.array(step_ms) * 1e3),
         "step_breakdown_us": {"form": float(np.mean(form_ms)) * 1e3, "pcg": float(np.mean(pcg_ms)) * 1e3,
                               "recover": float(np.mean(step_ms) - np.mean(form_ms) - np.mean(pcg_ms)) * 1e3},
@@ -408,9 +459,72 @@ def run_ours(args, rank, world, local_rank):
         "exit_sweep": exit_sweep, "precon_compare": precon_compare, "dense_cost": dense_cost,
         "nmpc": nmpc,
         "large_state": large,
+        "dot_fp64": dot64,
     }
+    line["summary"] = summarize(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def summarize(line):
+    """The secondary figures in a few keys, last in the line (a reader of its
+    tail sees them)."""
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+    out = {"us_per_solve_N512": line["value"], "e2e_us": g(line, "e2e", "value"),
+           "pcg_us": g(line, "step_breakdown_us", "pcg"), "iters": g(line, "pcg_iters", "mean"),
+           "sync_latency_frac": g(line, "roofline", "frac"), "hbm_frac": g(line, "roofline", "hbm", "frac"),
+           "parity_lambda": g(line, "parity", "err_lambda"), "parity_dz": g(line, "parity", "err_dz"),
+           "dot_fp64_us": g(line, "dot_fp64", "pcg_us"), "dot_fp64_err_lambda": g(line, "dot_fp64", "err_lambda"),
+           "batched_solves_per_s": g(line, "batched", "solves_per_s"),
+           "batched_loop_solves_per_s": g(line, "batched", "loop_solves_per_s"),
+           "batched_speedup_vs_loop": g(line, "batched", "speedup_vs_loop"),
+           "backward_fwd_ms": g(line, "backward", "fwd_ms"), "backward_bwd_ms": g(line, "backward", "bwd_ms"),
+           "backward_grad_err": g(line, "backward", "grad_relerr_vs_oracle"),
+           "large_fwd_ms": g(line, "large_state", "fwd_ms"), "large_bwd_ms": g(line, "large_state", "bwd_ms"),
+           "large_err_lambda": g(line, "large_state", "err_lambda_vs_oracle", "max"),
+           "large_grad_err": g(line, "large_state", "grad_err_vs_oracle", "max"),
+           "large_pcg_hbm_frac": g(line, "large_state", "pcg_roofline_fwd", "frac")}
+    sw = g(line, "sweep", "per_N") or {}
+    out["sweep_p50_us"] = {k: g(v, "us_per_solve", "p50") for k, v in sw.items()}
+    return out
+
+
+def run_dot64(s, dev, lq, lam0, flush, steps, us_default, iters_default):
+    """The measured workload with the PCG dot products accumulated in FP64
+    instructions (opts.dot = 1) instead of float pairs: µs per PCG solve,
+    iterations and parity, beside the default."""
+    import torch
+    import oracle
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    lt = LQTensors.from_numpy(lq, device=dev)
+    sch = s.alloc_schur(lt)
+    s.form(lt, sch)
+    o = make_opts(tol=1e-6, dot=1)
+    stream = torch.cuda.current_stream(dev)
+    lams = [t.clone() for t in lam0[:steps + 3]]
+    stats = s.alloc_stats(len(lams), dev)
+    for i in range(3):
+        s.pcg_solve(lt, sch, lams[i], o, stats[i * 24:(i + 1) * 24])
+    torch.cuda.synchronize()
+    tim = _step_timer(s, stream)
+    for i in range(3, len(lams)):
+        flush.zero_()
+        tim(lambda: s.pcg_solve(lt, sch, lams[i], o, stats[i * 24:(i + 1) * 24]))
+    torch.cuda.synchronize()
+    st = read_stats(stats)[3:]
+    us = np.array(tim.ms()) * 1e3
+    lo, _, _ = oracle.kkt_solve(lq.astype(np.float64))
+    err = oracle.relerr(lams[-1].cpu().double().numpy(), lo)
+    return {"workload": f"the N={lq.N} warm-started solve, PCG only, {len(us)} solves",
+            "pcg_us": float(np.median(us)), "us_pct": pct(us), "iters_mean": float(np.mean(st["iters"])),
+            "converged": bool(np.all(st["status"] == 0)), "err_lambda": err,
+            "default_pcg_us": us_default, "default_iters_mean": iters_default,
+            "slowdown_vs_default": float(np.median(us)) / us_default}
 
 
 def run_e2e(s, lq, lam0, opts, dev, flush, steps, warmup):
@@ -609,6 +723,14 @@ def run_backward(s, dev, reps=5):
     it_f = read_stats(st)["iters"].astype(np.float64)
     it_b = read_stats(bst)["iters"].astype(np.float64)
     alg = float(np.sum(it_f + it_b)) * c["N"] * pcg_bytes_per_knot_iter(c["nx"])
+    # the batch's clusters keep their operators on chip: the floor is the
+    # reductions' latency, 2 exchanges per iteration on each cluster, the
+    # instances spread over the co-resident clusters
+    sh = s.pcg_shape(lt, sch, opts)
+    lat = None
+    if sh["form"] == "cluster":
+        x = s.bench_exchange(sh["C"], sh["threads"] // 32, rounds=1000)
+        lat = float(np.sum(it_f + it_b)) * 2.0 * x["ns"] * 1e-6 / max(1, min(sh["clusters"], c["B"]))
     # gradient of instance 0 against the oracle's analytic gradient
     it0 = batch.items[0].astype(np.float64)
     l0, x0, u0 = oracle.kkt_solve(it0)
@@ -636,8 +758,11 @@ def run_backward(s, dev, reps=5):
     return {"workload": f"{c['B']} instances x N={c['N']} (nx={c['nx']}, nu={c['nu']}), loss sum ||dz||^2 + w^T lambda",
             "fwd_ms": f, "bwd_ms": bw, "bwd_over_fwd": bw / f, "loop_fwd_bwd_ms": t_loop,
             "speedup_vs_loop": t_loop / (f + bw), "converged": ok, "grad_relerr_vs_oracle": gerr,
-            "pcg_roofline": {"bound": "hbm", "note": "forward and adjoint PCG bytes over fwd + bwd time",
-                             "frac": alg / ((f + bw) / 1e3) / 1e9 / hbm, "peak_source": note}}
+            "pcg_roofline": {"bound": "sync_latency", "frac": (lat / (f + bw)) if lat else None,
+                             "floor_ms": lat, "shape": sh,
+                             "note": "forward + adjoint PCG iterations x 2 measured exchanges, spread over the "
+                                     "co-resident clusters, over fwd + bwd time",
+                             "hbm_equivalent_frac": alg / ((f + bw) / 1e3) / 1e9 / hbm, "peak_source": note}}
 
 
 def _step_timer(s, stream):
@@ -704,10 +829,10 @@ def run_sweep(s, dev, reps, flush):
         pus = np.array(pcg.ms()) * 1e3
         it = st["iters"].astype(np.float64)
         ach = float(np.mean(it)) * N * pcg_bytes_per_knot_iter(c["nx"]) / (np.mean(pus) * 1e-6) / 1e9
+        rl = latency_roofline(s, lt, sch, opts, float(np.mean(it)), float(np.median(pus)), rounds=1000)
+        rl["hbm"] = {"achieved_gbs": ach, "frac": ach / hbm, "peak_source": note}
         out[str(N)] = {"us_per_solve": pct(us), "pcg_us": float(np.median(pus)),
-                       "iters": pct(it), "converged": bool(np.all(st["status"] == 0)),
-                       "roofline": {"bound": "hbm", "achieved_gbs": ach, "frac": ach / hbm,
-                                    "peak_source": note}}
+                       "iters": pct(it), "converged": bool(np.all(st["status"] == 0)), "roofline": rl}
     return {"workload": f"single instances N in {list(c['Ns'])}, nx={c['nx']}, nu={c['nu']}, "
                         f"{reps} warm solves each (L2 flushed before each)", "per_N": out}
 
@@ -908,7 +1033,7 @@ def run_large(s, dev, solves, B=None):
     N_i ~ U{64..256}, dt = 0.005, Qd ~ U[0.1, 100].  One step = `solves`
     warm-started forward solves (each with one refinement step) through the
     autograd Function and the backward of loss sum ||dz||^2 + w^T lambda over
-    all of them.  The PCG launch plan comes from the autotuner (single-launch
+    all of them (each adjoint solve with one refinement step too).  The PCG launch plan comes from the autotuner (single-launch
     plans, so the same launch serves refinement and the adjoint solve)."""
     import torch
     import oracle
@@ -961,6 +1086,23 @@ def run_large(s, dev, solves, B=None):
     picks = sorted({int(np.argmin(Ns)), int(np.argmax(Ns))} | set(range(0, batch.B, 128)))
     errs = {int(b): oracle.relerr(lam_l[ko[b]:ko[b + 1]], oracle.kkt_solve(batch.items[b].astype(np.float64))[0])
             for b in picks}
+    # gradient of the summed loss w.r.t. each sampled instance's inputs against
+    # the oracle's analytic gradient (field by field, max over fields); the
+    # loss terms of the `solves` solves add, and every solve reaches the same
+    # (lambda, dz) up to the solve's error, so the oracle gradient is
+    # `solves` times the one-solve gradient
+    co = batch.ctrl_off()
+    gerrs = {}
+    for b in picks[:4]:
+        it64 = batch.items[b].astype(np.float64)
+        lo_, xo_, uo_ = oracle.kkt_solve(it64)
+        go = oracle.grad(it64, lo_, xo_, uo_, w[ko[b]:ko[b + 1]].double().cpu().numpy(), 2 * xo_, 2 * uo_)
+        e = 0.0
+        for f in LQTensors.FIELDS:
+            sl = slice(co[b], co[b + 1]) if f in ("A", "B", "Rd", "r") else slice(ko[b], ko[b + 1])
+            gf = leaves[f].grad[sl].double().cpu().numpy()
+            e = max(e, oracle.relerr(gf, solves * go[f]))
+        gerrs[int(b)] = e
     n = batch.B * solves
     hbm, note = hbm_peak()
     it = sts["iters"].astype(np.float64)
@@ -973,6 +1115,10 @@ def run_large(s, dev, solves, B=None):
             "solves_per_s_fwd_bwd": n / ((fwd_ms + bwd_ms) / 1e3),
             "iters_first_pcg": pct(it), "converged": bool(np.all(sts["status"] == 0)),
             "err_lambda_vs_oracle": {"max": max(errs.values()), "instances": len(errs)},
+            "grad_err_vs_oracle": {"max": max(gerrs.values()), "per_instance": gerrs,
+                                   "note": "every gradient field against the oracle's analytic gradient "
+                                           "(normwise per field, max over fields); forward and adjoint "
+                                           "solves each with one refinement step"},
             "pcg_roofline_fwd": {"bound": "hbm", "note": "first PCG of each solve only, over the whole forward time",
                                  "achieved_gbs": alg / (fwd_ms / 1e3) / 1e9,
                                  "frac": alg / (fwd_ms / 1e3) / 1e9 / hbm, "peak_source": note},

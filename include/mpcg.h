@@ -234,6 +234,19 @@ int mpcg_pcg_solve(mpcg_handle *h, mpcg_dims dims, const mpcg_schur *schur, void
                    const mpcg_opts *opts, mpcg_stats *stats, void *stream);
 
 /*
+ * The launch shape mpcg_pcg_solve[_batched] uses for these arguments (the
+ * same choice, made once and cached on the handle; nothing is launched):
+ * shape[0] = kernel form (0 a thread-block cluster per instance, 1 one CTA
+ * per instance reading the blocks from L2, 2 the tiled kernel streaming
+ * TMA tiles), shape[1] = CTAs per cluster, shape[2] = clusters (or CTAs) in
+ * the grid, shape[3] = threads per CTA.  `shape` is a HOST int[4]; the
+ * schur pointers matter only through their alignment (the tiled kernel
+ * needs 16-byte-aligned blocks).  B = 1 for a single instance.
+ */
+int mpcg_pcg_shape(mpcg_handle *h, mpcg_dims dims, int B, const mpcg_schur *schur,
+                   const mpcg_opts *opts, int *shape);
+
+/*
  * Primal step (Eq. schur): dz = -G^-1 (g - C^T lambda), i.e.
  *   dx_k = (lambda_k - A_k^T lambda_{k+1} - q_k) / Qd_k   (k < N-1)
  *   dx_{N-1} = (lambda_{N-1} - q_{N-1}) / Qd_{N-1}
@@ -321,14 +334,15 @@ int mpcg_backward(mpcg_handle *h, mpcg_dims dims, const mpcg_lq *lq, const mpcg_
  * the scratch that mpcg_backward_batched takes as `workspace` (the adjoint
  * right-hand side, the adjoint solution and the instance queue:
  * mpcg_workspace_bytes(dims, B) bytes) comes instead from one fixed array
- * of MPCG_NOALLOC_SCRATCH_BYTES bytes of device memory that the library
- * reserves when it is loaded; every GPU that loads the library keeps that
- * array until the process exits.
+ * of MPCG_NOALLOC_SCRATCH_BYTES bytes of device memory.  mpcg_create
+ * reserves it on the handle's device (looking up its address there, which
+ * under CUDA's lazy module loading is what commits it), so a device that
+ * has not that much memory free fails at mpcg_create, not inside this call;
+ * every GPU that gets a handle keeps the array until the process exits.
  *
  * Arguments, layouts and results are those of mpcg_backward_batched
  * (knot_off may be NULL when B == 1).  Behaviour specific to this call:
- *  - the first call on a device looks up the array's device address with
- *    that device current; make that first call before any stream capture;
+ *  - the handle must belong to the current device (else MPCG_EINVAL);
  *  - a problem whose scratch exceeds MPCG_NOALLOC_SCRATCH_BYTES is refused
  *    with MPCG_ETOOLARGE before anything is launched;
  *  - it calls no cudaMalloc, cudaFree or allocating library routine;
@@ -432,6 +446,21 @@ int mpcg_selftest_wait(mpcg_handle *h, int push, double limit_s, int *status, vo
  * its wait to its exit (well below limit_s when the flag released it). */
 int mpcg_selftest_drain(mpcg_handle *h, int mode, double limit_s, int *status,
                         unsigned long long *elapsed_ns, void *stream);
+
+/* Microbenchmark of the PCG kernels' cluster reduction (not in the paper;
+ * the latency floor that the single-instance solve is measured against).
+ * One cluster of C CTAs x W warps (1 <= C, W <= 16; else MPCG_EINVAL) runs
+ * `rounds` (1..10^6) rounds of the two exchanges of a PCG iteration
+ * (Algorithm 1's two reductions) exactly as the float32 cluster kernel
+ * performs them -- halo pushes from the boundary warps, a shuffle sum per
+ * warp, warp 0 combining the warp sums and pushing the CTA sum into every
+ * CTA with st.async, a bounded mbarrier wait, a CTA barrier and the sum of
+ * the C partials -- with no other arithmetic.  DEVICE outputs: out[0] =
+ * SM clock cycles and out[1] = nanoseconds over all rounds (CTA 0), so one
+ * exchange takes out / (2 rounds); status[C] = MPCG_CONVERGED per CTA, or
+ * MPCG_TIMEOUT if a wait gave up (after 1 s). */
+int mpcg_bench_exchange(mpcg_handle *h, int C, int W, int rounds, unsigned long long *out,
+                        int *status, void *stream);
 
 #ifdef __cplusplus
 }

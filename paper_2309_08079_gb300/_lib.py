@@ -35,7 +35,7 @@ EXPORTS = (
     "mpcg_backward_batched_noalloc", "mpcg_refine_step", "mpcg_refine_step_batched",
     "mpcg_linearize", "mpcg_linearize_batched", "mpcg_line_search", "mpcg_line_search_batched",
     "mpcg_form_schur_precon", "mpcg_form_schur_precon_batched", "mpcg_selftest_wait",
-    "mpcg_selftest_drain",
+    "mpcg_selftest_drain", "mpcg_pcg_shape", "mpcg_bench_exchange",
 )
 
 
@@ -155,6 +155,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.mpcg_selftest_wait.argtypes = [vp, i32, C.c_double, vp, vp]
     lib.mpcg_selftest_drain.restype = i32
     lib.mpcg_selftest_drain.argtypes = [vp, i32, C.c_double, vp, vp, vp]
+    lib.mpcg_pcg_shape.restype = i32
+    lib.mpcg_pcg_shape.argtypes = [vp, mpcg_dims, i32, P(mpcg_schur), P(mpcg_opts), P(i32)]
+    lib.mpcg_bench_exchange.restype = i32
+    lib.mpcg_bench_exchange.argtypes = [vp, i32, i32, i32, vp, vp, vp]
     _lib = lib
     return lib
 

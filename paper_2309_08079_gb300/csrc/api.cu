@@ -245,29 +245,34 @@ int form_schur_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off,
     return err_cuda(launch_form_schur<T>(a, st));
 }
 
+// The launch shape of a PCG call (chosen once per shape key, then cached).
+template <typename T>
+int pcg_shape_t(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, const mpcg_schur *s,
+                PcgLaunch &L) {
+    if (o && (o->refine < 0 || o->dot < 0 || o->dot > 1)) return MPCG_EINVAL;
+    std::lock_guard<std::mutex> g(h->mu);
+    // the tiled kernel's eligibility depends on pointer alignment
+    const int aligned = (((uintptr_t)s->Sd | (uintptr_t)s->So | (uintptr_t)s->Pd | (uintptr_t)s->Po) % 16) == 0;
+    const int tickets = (o && o->instances && o->n_instances > 0) ? o->n_instances : B;
+    auto key = std::make_tuple(d.dtype, d.nx, d.N, tickets,
+                               (o ? o->cluster : 0) | ((o ? o->mode : 0) << 8) | (aligned << 16) |
+                                   ((o ? o->dot : 0) << 17));
+    auto it = h->shapes.find(key);
+    if (it != h->shapes.end()) {
+        L = it->second;
+        return MPCG_OK;
+    }
+    const int rc = choose_pcg<T>(h, d, tickets, o, s, L);
+    if (rc == MPCG_OK) h->shapes.emplace(key, L);
+    return rc;
+}
+
 template <typename T>
 int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const mpcg_schur *s,
           const T *rhs, T sign, T *lam, const mpcg_opts *o, mpcg_stats *stats, void *ws,
           cudaStream_t st) {
-    if (o && (o->refine < 0 || o->dot < 0 || o->dot > 1)) return MPCG_EINVAL;
     PcgLaunch L{};
-    int rc = MPCG_OK;
-    {
-        std::lock_guard<std::mutex> g(h->mu);
-        // the tiled kernel's eligibility depends on pointer alignment
-        const int aligned = (((uintptr_t)s->Sd | (uintptr_t)s->So | (uintptr_t)s->Pd | (uintptr_t)s->Po) % 16) == 0;
-        const int tickets = (o && o->instances && o->n_instances > 0) ? o->n_instances : B;
-        auto key = std::make_tuple(d.dtype, d.nx, d.N, tickets,
-                                   (o ? o->cluster : 0) | ((o ? o->mode : 0) << 8) | (aligned << 16) |
-                                       ((o ? o->dot : 0) << 17));
-        auto it = h->shapes.find(key);
-        if (it != h->shapes.end()) {
-            L = it->second;
-        } else {
-            rc = choose_pcg<T>(h, d, tickets, o, s, L);
-            if (rc == MPCG_OK) h->shapes.emplace(key, L);
-        }
-    }
+    int rc = pcg_shape_t<T>(h, d, B, o, s, L);
     if (rc) return rc;
     PcgParams<T> P;
     P.nx = d.nx;
@@ -443,6 +448,9 @@ bool lq_ok(const mpcg_lq *lq, const mpcg_dims &d) {
     return d.N == 1 || (lq->A && lq->B && lq->Rd && lq->r);
 }
 
+// below: resolves the no-allocation scratch on the handle's device
+int noalloc_setup(mpcg_handle *h);
+
 }  // namespace
 
 extern "C" {
@@ -483,6 +491,14 @@ int mpcg_create(mpcg_handle **out) {
         cudaGetLastError();
         delete h;
         return MPCG_ECUDA;
+    }
+    // the no-allocation backward's scratch array is committed here, not on
+    // that entry point's first call (under lazy module loading the array's
+    // module loads, and its memory is reserved, when its address is first
+    // looked up)
+    if (int rc = noalloc_setup(h)) {
+        delete h;
+        return rc;
     }
     *out = h;
     return MPCG_OK;
@@ -543,6 +559,19 @@ int mpcg_pcg_solve_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_o
         return MPCG_EINVAL;
     return DISPATCH(d, solve_t, h, d, B, knot_off, s, lambda, opts, stats, workspace,
                     (cudaStream_t)stream);
+}
+
+int mpcg_pcg_shape(mpcg_handle *h, mpcg_dims d, int B, const mpcg_schur *s, const mpcg_opts *opts,
+                   int *shape) {
+    if (!h || !dims_ok(d) || B < 1 || !s || !shape) return MPCG_EINVAL;
+    PcgLaunch L{};
+    const int rc = DISPATCH(d, pcg_shape_t, h, d, B, opts, s, L);
+    if (rc) return rc;
+    shape[0] = L.cta_mode;
+    shape[1] = L.C;
+    shape[2] = L.clusters;
+    shape[3] = L.threads;
+    return MPCG_OK;
 }
 
 int mpcg_pcg_solve(mpcg_handle *h, mpcg_dims d, const mpcg_schur *s, void *lambda,
@@ -619,10 +648,10 @@ int mpcg_backward(mpcg_handle *h, mpcg_dims d, const mpcg_lq *lq, const mpcg_sch
 // ---------------------------------------------------------------------------
 // Backward pass without a workspace, for callers that cannot allocate device
 // memory when they differentiate (see mpcg_backward_batched_noalloc in
-// include/mpcg.h).  Its scratch is this one file-scope array, reserved when
-// the library is loaded.  Host code cannot use the array's name as a device
-// address, so the address is looked up once per device with
-// cudaGetSymbolAddress while that device is current.
+// include/mpcg.h).  Its scratch is this one file-scope array.  Host code
+// cannot use the array's name as a device address, so mpcg_create looks the
+// address up once per device with cudaGetSymbolAddress while that device is
+// current (which also loads the array's module and reserves its memory).
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MPCG_NOALLOC_SCRATCH_BYTES];
 
@@ -649,6 +678,11 @@ int noalloc_scratch(mpcg_handle *h, void **out) {
     }
     *out = g_noalloc_addr[dev];
     return MPCG_OK;
+}
+
+int noalloc_setup(mpcg_handle *h) {
+    void *p = nullptr;
+    return noalloc_scratch(h, &p);
 }
 }  // namespace
 

@@ -79,10 +79,140 @@ drain_selftest_kernel(int mode, uint64_t limit_ns, int *status, unsigned long lo
     if (!gave_up) cluster_sync_all();  // no CTA leaves while a peer may still write to it
 }
 
+// The cluster all-reduce of the PCG kernels with nothing else around it: the
+// latency floor of one reduction of Algorithm 1 on a given launch shape.
+// Per exchange, as the float32 kernels do it: boundary warps push a 64-byte
+// halo slot to each neighbour, every warp sums its lanes (shuffle
+// butterfly of float pairs), warp 0 sums the warp partials (named barrier)
+// and pushes the CTA partial into every CTA, one thread waits (bounded) for
+// the C partials and the halos, a CTA barrier, every warp sums the C slots.
+// Exchanges A and B alternate on their own buffers, as in the kernels.
+constexpr int XB_CMAX = 16, XB_WMAX = 16;
+struct XbenchSmem {
+    dfloat slot[2][XB_CMAX];
+    dfloat wpart[2][XB_WMAX];
+    float halo[2][32];
+    uint64_t mb[3];  // exchange A, exchange B, peers stopped
+    int abort_flag;
+};
+
+__device__ __forceinline__ dfloat xb_butterfly(dfloat v, int width) {
+    for (int m = width >> 1; m >= 1; m >>= 1) v = df_add_lazy(v, Acc<float>::shfl_xor(v, m));
+    return v;
+}
+
+__global__ void __launch_bounds__(512, 1)
+exchange_bench_kernel(int rounds, uint64_t limit_ns, int *status, unsigned long long *out) {
+    __shared__ __align__(16) XbenchSmem S;
+    const uint32_t C = cluster_size(), rank = cluster_rank();
+    const int tid = threadIdx.x, nthreads = blockDim.x, W = nthreads / 32;
+    const uint32_t warp = tid / 32, lane = tid % 32;
+    int wpow = 1, cpow = 1;
+    while (wpow < W) wpow <<= 1;
+    while (cpow < (int)C) cpow <<= 1;
+    const bool has_left = rank > 0, has_right = rank + 1 < C;
+    if (tid == 0) {
+        mbar_init(smem_u32(&S.mb[0]), 1);
+        mbar_init(smem_u32(&S.mb[1]), 1);
+        mbar_init(smem_u32(&S.mb[2]), C > 1 ? C - 1 : 1);
+        S.abort_flag = 0;
+        fence_mbar_init();
+    }
+    cluster_sync_all();
+    const uint32_t peer = lane < C ? lane : 0;
+    const uint32_t halo_bytes = 64u * ((has_left ? 1u : 0u) + (has_right ? 1u : 0u));
+    uint32_t ph[2] = {0u, 0u};
+    int fail = 0;
+    dfloat v{1e-3f * (float)(tid + 1), 0.f};
+    const unsigned long long c0 = clock64();
+    const uint64_t g0 = global_ns();
+    for (int r = 0; r < rounds && !fail; ++r) {
+        for (int x = 0; x < 2 && !fail; ++x) {
+            const uint32_t mb = smem_u32(&S.mb[x]);
+            // halo slots: the first warp to the left neighbour, the last to the right
+            if (lane < 4) {
+                if (has_left && warp == 0)
+                    st_async_v4(map_rank(smem_u32(&S.halo[x][16 + 4 * lane]), rank - 1), v.hi, v.lo, 0.f, 0.f,
+                                map_rank(mb, rank - 1));
+                if (has_right && (int)warp == W - 1)
+                    st_async_v4(map_rank(smem_u32(&S.halo[x][4 * lane]), rank + 1), v.hi, v.lo, 0.f, 0.f,
+                                map_rank(mb, rank + 1));
+            }
+            const dfloat w = xb_butterfly(v, 32);
+            if (lane == 0) S.wpart[x][warp] = w;
+            if (warp == 0) {
+                named_bar_sync(1, nthreads);
+                const int q = (int)lane & (wpow - 1);
+                const dfloat y = xb_butterfly(q < W ? S.wpart[x][q] : dfloat{0.f, 0.f}, wpow);
+                if (lane < C) st_async(map_rank(smem_u32(&S.slot[x][rank]), peer), y, map_rank(mb, peer));
+            } else {
+                named_bar_arrive(1, nthreads);
+            }
+            int f = 0;
+            if (tid == 0) {
+                mbar_arrive_expect(mb, C * (uint32_t)sizeof(dfloat) + halo_bytes);
+                f = !mbar_wait_bounded_abort(mb, ph[x], limit_ns, &S.abort_flag);
+            }
+            ph[x] ^= 1u;
+            if (__syncthreads_or(f)) fail = 1;
+            const int q = (int)lane & (cpow - 1);
+            const dfloat t = xb_butterfly(q < (int)C ? S.slot[x][q] : dfloat{0.f, 0.f}, cpow);
+            v.lo = __fmaf_rn(t.hi, 1e-12f, v.lo);
+        }
+    }
+    const unsigned long long c1 = clock64();
+    const uint64_t g1 = global_ns();
+    if (tid == 0) {
+        status[rank] = fail ? MPCG_TIMEOUT : MPCG_CONVERGED;
+        if (rank == 0) {
+            out[0] = c1 - c0;
+            out[1] = g1 - g0;
+            out[2] = (unsigned long long)__float_as_uint(v.hi);  // keeps the arithmetic live
+        }
+    }
+    if (fail) {
+        if (tid == 0)
+            cluster_drain(rank, C, smem_u32(&S.abort_flag), smem_u32(&S.mb[2]), limit_ns, 20000ull);
+        __syncthreads();
+        return;
+    }
+    cluster_sync_all();  // no CTA leaves while a peer may still write to it
+}
+
 }  // namespace
 }  // namespace mpcg
 
 using namespace mpcg;
+
+extern "C" int mpcg_bench_exchange(mpcg_handle *h, int C, int W, int rounds, unsigned long long *out,
+                                   int *status, void *stream) {
+    if (!h || !out || !status || C < 1 || C > XB_CMAX || W < 1 || W > XB_WMAX || rounds < 1 ||
+        rounds > 1000000)
+        return MPCG_EINVAL;
+    if (cudaFuncSetAttribute(exchange_bench_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return MPCG_ECUDA;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(32 * W, 1, 1);
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, exchange_bench_kernel, rounds, (uint64_t)1000000000ull,
+                                             status, out);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MPCG_ECUDA;
+    }
+    return MPCG_OK;
+}
 
 extern "C" int mpcg_selftest_drain(mpcg_handle *h, int mode, double limit_s, int *status,
                                    unsigned long long *elapsed_ns, void *stream) {

@@ -176,6 +176,37 @@ class Solver:
     def alloc_workspace(self, lq: LQTensors) -> torch.Tensor:
         return torch.zeros(self.workspace_bytes(lq), dtype=torch.uint8, device=lq.device)
 
+    # ---------------------------------------------------------------- introspection
+    def pcg_shape(self, lq: LQTensors, schur: SchurTensors, opts=None, N: Optional[int] = None) -> dict:
+        """The launch shape pcg_solve uses for these arguments (nothing is
+        launched): kernel form, CTAs per cluster, clusters in the grid,
+        threads per CTA."""
+        ss = schur.struct()
+        o = opts if opts is not None else make_opts()
+        dims = lq.dims()
+        if N is not None:
+            dims.N = int(N)
+        shape = (C.c_int * 4)()
+        L.check("mpcg_pcg_shape", self.lib.mpcg_pcg_shape(self.h, dims, lq.nb, C.byref(ss), C.byref(o), shape))
+        return {"form": ("cluster", "cta_l2", "cta_tma")[shape[0]], "C": shape[1], "clusters": shape[2],
+                "threads": shape[3]}
+
+    def bench_exchange(self, C_: int, W: int, rounds: int = 2000, stream=None) -> dict:
+        """Latency of one cluster reduction of the PCG kernels (both of
+        Algorithm 1's per-iteration reductions take one) on a C_ x W launch
+        shape, from mpcg_bench_exchange: cycles and nanoseconds per
+        exchange."""
+        out = torch.zeros(3, dtype=torch.int64, device=self.device)
+        st = torch.full((C_,), -1, dtype=torch.int32, device=self.device)
+        L.check("mpcg_bench_exchange", self.lib.mpcg_bench_exchange(self.h, int(C_), int(W), int(rounds),
+                                                                  _ptr(out), _ptr(st), _stream(stream)))
+        torch.cuda.synchronize(self.device)
+        if not bool((st == 0).all()):
+            raise RuntimeError(f"mpcg_bench_exchange: a wait gave up ({st.tolist()})")
+        o = out.cpu().tolist()
+        return {"cycles": o[0] / (2.0 * rounds), "ns": o[1] / (2.0 * rounds), "C": int(C_), "W": int(W),
+                "rounds": int(rounds)}
+
     # ---------------------------------------------------------------- the path
     def form_schur(self, lq: LQTensors, schur: SchurTensors, stream=None) -> SchurTensors:
         ls, ss = lq.lq_struct(), schur.struct()

@@ -452,6 +452,45 @@ def test_give_up_drains_the_cluster():
     assert stt["status"][0] == 0 and e_lam < TOL_F32 and e_dz < TOL_F32
 
 
+@pytest.mark.parametrize("N,form", [(512, "cluster"), (128, "cluster"), (600, "cta_l2")])
+def test_pcg_shape_reports_the_launch(N, form):
+    """mpcg_pcg_shape reports the launch shape a solve uses: a 16-CTA
+    cluster of 256 threads (32 knots x 8 lanes) at N = 512; the CTA kernel
+    beyond a cluster's 512 register-resident knots."""
+    from paper_2309_08079_gb300.solver import LQTensors
+    s = solver()
+    lt = LQTensors.from_numpy(gen.kuka_lq(14, 7, N, 1).astype(np.float32))
+    sh = s.pcg_shape(lt, s.alloc_schur(lt))
+    assert sh["form"] == form, sh
+    if N == 512:
+        assert sh["C"] == 16 and sh["threads"] == 256
+    if form == "cluster":
+        assert sh["C"] * sh["threads"] // 8 >= N  # 8 lanes per knot
+
+
+def test_exchange_microbenchmark():
+    """mpcg_bench_exchange runs the cluster reduction of the PCG kernels on a
+    given shape and reports its time; every wait completes, one exchange
+    takes a fraction of a microsecond to a few microseconds, and a 16-CTA
+    cluster is no faster than a 2-CTA one."""
+    s = solver()
+    r16 = s.bench_exchange(16, 8, rounds=500)
+    r2 = s.bench_exchange(2, 2, rounds=500)
+    assert 50 < r16["ns"] < 5000 and 50 < r2["ns"] < 5000, (r16, r2)
+    assert r16["ns"] >= 0.8 * r2["ns"], (r16, r2)
+    assert r16["cycles"] > 100
+
+
+def test_exchange_microbenchmark_arguments_are_checked():
+    import torch
+    from paper_2309_08079_gb300._lib import MPCG_EINVAL
+    s = solver()
+    out = torch.zeros(3, dtype=torch.int64, device="cuda")
+    st = torch.zeros(16, dtype=torch.int32, device="cuda")
+    for C_, W, r in ((0, 8, 10), (17, 8, 10), (16, 0, 10), (16, 17, 10), (16, 8, 0)):
+        assert s.lib.mpcg_bench_exchange(s.h, C_, W, r, out.data_ptr(), st.data_ptr(), None) == MPCG_EINVAL
+
+
 def test_drain_selftest_arguments_are_checked():
     import torch
     from paper_2309_08079_gb300._lib import MPCG_EINVAL

@@ -23,12 +23,17 @@ pytestmark = pytest.mark.gpu
 FIELDS = ("A", "B", "Qd", "Rd", "q", "r", "c")
 
 
-def _noalloc_backward(s, lt, sch, lam, dx, du, lam_bar, dx_bar, du_bar, opts):
+def _noalloc_outputs(s, lt):
+    import torch
+    g = {f: torch.full_like(getattr(lt, f), float("nan")) for f in FIELDS}
+    return g, s.alloc_stats(lt.nb)
+
+
+def _noalloc_backward(s, lt, sch, lam, dx, du, lam_bar, dx_bar, du_bar, opts, outputs=None):
     import torch
     from paper_2309_08079_gb300 import _lib as L
-    g = {f: torch.full_like(getattr(lt, f), float("nan")) for f in FIELDS}
+    g, stats = outputs if outputs is not None else _noalloc_outputs(s, lt)
     gs = L.mpcg_grads(*(g[f].data_ptr() for f in FIELDS))
-    stats = s.alloc_stats(lt.nb)
     ls, ss = lt.lq_struct(), sch.struct()
     ptr = lambda t: C.c_void_p(t.data_ptr())
     ko = None if lt.knot_off is None else ptr(lt.knot_off)
@@ -50,13 +55,22 @@ def test_noalloc_backward_matches_workspace_backward_on_two_calls():
     lam, dx, du, st, sch = s.solve(lt, opts=opts, workspace=s.alloc_workspace(lt))
     K = lt.total
     seeds = [(gen.loss_weights(K * 14, 40), 2.0, 2.0), (-gen.loss_weights(K * 14, 41), 1.0, 3.0)]
+    keep = []  # every call's tensors stay alive, so the allocator's count moves only by new allocations
     for call, (w, ax, au) in enumerate(seeds):
         lam_bar = torch.as_tensor(w.reshape(K, 14), dtype=torch.float32, device="cuda")
         dx_bar = (ax * dx).contiguous()
         du_bar = (au * du).contiguous()
         ref, st_ref = s.backward(lt, sch, lam, dx, du, lam_bar, dx_bar, du_bar, opts=opts)
-        new, st_new = _noalloc_backward(s, lt, sch, lam, dx, du, lam_bar, dx_bar, du_bar, opts)
+        outs = _noalloc_outputs(s, lt)
         torch.cuda.synchronize()
+        free0, used0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+        new, st_new = _noalloc_backward(s, lt, sch, lam, dx, du, lam_bar, dx_bar, du_bar, opts, outs)
+        torch.cuda.synchronize()
+        if call == 1:
+            # the second call allocates nothing: neither device memory at the
+            # driver level nor through the caller's allocator
+            assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == used0
+        keep.append((lam_bar, dx_bar, du_bar, ref, st_ref, outs, new, st_new))
         assert np.all(read_stats(st_new)["status"] == 0), (call, read_stats(st_new))
         assert np.array_equal(read_stats(st_new)["iters"], read_stats(st_ref)["iters"])
         for f in FIELDS:
