@@ -152,6 +152,13 @@ typedef struct {
        FP64 pipe is a small fraction of its FP32 rate).  float64 always
        accumulates in float64.  Other values: MPCG_EINVAL. */
     int dot;
+    /* Exit tolerance (relative residual, the correction's own right-hand
+       side) of the correction solves of iterative refinement
+       (mpcg_refine_step*, and the backward's opts.refine steps).  <= 0: tol.
+       The correction only has to shrink an error already at the float32
+       floor of S+, so a loose test (1e-3) reaches the same result in about
+       half the iterations of 1e-6. */
+    double refine_tol;
 } mpcg_opts;
 
 typedef struct {
@@ -262,7 +269,8 @@ int mpcg_recover_step(mpcg_handle *h, mpcg_dims dims, const mpcg_lq *lq, const v
  *     b - S+ lambda = -(C dz(lambda) + c),   dz(lambda) = G^-1 (C^T lambda - g),
  * is formed per knot in extended precision from the inputs `lq` (not from
  * the stored S+), the correction S+ d = residual is solved by PCG with the
- * same S+ and Phi^-1 from d = 0, and lambda += d.  `workspace` needs
+ * same S+ and Phi^-1 from d = 0 (exit test: relative residual
+ * opts->refine_tol, else opts->tol), and lambda += d.  `workspace` needs
  * mpcg_workspace_bytes(dims, B) bytes; `stats` (device) receives the
  * correction solve's stats (relres is relative to the residual).
  */

@@ -64,7 +64,7 @@ class mpcg_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("tol_mode", C.c_int), ("max_iter", C.c_int),
                 ("cluster", C.c_int), ("mode", C.c_int), ("instances", C.c_void_p),
                 ("n_instances", C.c_int), ("precon", C.c_int), ("refine", C.c_int),
-                ("dot", C.c_int)]
+                ("dot", C.c_int), ("refine_tol", C.c_double)]
 
 
 class mpcg_stats(C.Structure):

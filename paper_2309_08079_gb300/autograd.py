@@ -19,13 +19,18 @@ class MPCGSolve(torch.autograd.Function):
     @staticmethod
     def forward(ctx, A, B, Qd, Rd, q, r, c, lam0, cfg):
         """cfg: dict(solver, nx, nu, N, knot_off, nb, total, opts, workspace,
-        refine) -- refine = steps of iterative refinement after the PCG solve."""
+        refine, refine_tol) -- refine = steps of iterative refinement after the
+        forward and after the adjoint PCG solve; refine_tol = exit tolerance of
+        their correction solves (default: the solve's own)."""
         s = cfg["solver"]
         lq = LQTensors(cfg["nx"], cfg["nu"], cfg["N"], A.contiguous(), B.contiguous(),
                        Qd.contiguous(), Rd.contiguous(), q.contiguous(), r.contiguous(),
                        c.contiguous(), knot_off=cfg.get("knot_off"), nb=cfg.get("nb", 1),
                        total=cfg.get("total", cfg["N"]))
         opts = cfg.get("opts") or make_opts()
+        if cfg.get("refine_tol"):
+            opts = L.mpcg_opts.from_buffer_copy(opts)
+            opts.refine_tol = float(cfg["refine_tol"])
         lam = lam0.detach().clone() if lam0 is not None else torch.zeros(
             lq.total, lq.nx, dtype=lq.dtype, device=lq.device)
         lam, dx, du, stats, schur = s.solve(lq, lam, opts=opts, workspace=cfg.get("workspace"),

@@ -32,6 +32,19 @@ struct mpcg_handle {
 namespace {
 
 constexpr int kMaxThreads = 512;
+
+// Options of refinement's correction solves: the caller's, with the exit
+// test on the correction's own relative residual at refine_tol (if set).
+mpcg_opts correction_opts(const mpcg_opts *o) {
+    mpcg_opts c{};
+    if (o) c = *o;
+    else c.tol = 1e-6;
+    if (o && o->refine_tol > 0) {
+        c.tol = o->refine_tol;
+        c.tol_mode = 0;
+    }
+    return c;
+}
 constexpr int kMaxCluster = 16;
 
 inline int err_cuda(cudaError_t e) {
@@ -338,7 +351,8 @@ int backward_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, c
         // (a memset of the launch's Kgrid = B * N knots would overrun it)
         rc = err_cuda(launch_zero<T>(d.nx, bv, Kgrid, delta, st));
         if (rc) return rc;
-        rc = pcg_t<T>(h, d, B, knot_off, s, res, T(1), delta, o, nullptr, ws, st);
+        const mpcg_opts oc = correction_opts(o);
+        rc = pcg_t<T>(h, d, B, knot_off, s, res, T(1), delta, &oc, nullptr, ws, st);
         if (rc) return rc;
         rc = err_cuda(launch_axpy<T>(d.nx, bv, Kgrid, delta, mu, st));
         if (rc) return rc;
@@ -434,7 +448,8 @@ int refine_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, con
     if (rc) return rc;
     rc = err_cuda(cudaMemsetAsync(delta, 0, (size_t)Kgrid * d.nx * sizeof(T), st));
     if (rc) return rc;
-    rc = pcg_t<T>(h, d, B, knot_off, s, res, T(1), delta, o, stats, ws, st);
+    const mpcg_opts oc = correction_opts(o);
+    rc = pcg_t<T>(h, d, B, knot_off, s, res, T(1), delta, &oc, stats, ws, st);
     if (rc) return rc;
     return err_cuda(launch_axpy<T>(d.nx, bv, Kgrid, delta, lam, st));
 }

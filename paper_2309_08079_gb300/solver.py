@@ -115,7 +115,7 @@ class SchurTensors:
 
 
 def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0, mode=0, instances=None,
-              precon=0, refine=0, dot=0) -> L.mpcg_opts:
+              precon=0, refine=0, dot=0, refine_tol=0.0) -> L.mpcg_opts:
     """mode: 0 automatic, 1 cluster per instance, 2 one CTA per instance
     reading blocks from L2, 3 one CTA per instance streaming TMA tiles (as 2
     when blocks are not 16-byte multiples), 4 cluster per instance with
@@ -124,9 +124,10 @@ def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0, mode=0, instances=Non
     (Sec. IV-A), 1 block Jacobi, 2 the non-symmetric stair preconditioner
     (comparison only: no convergence guarantee).  refine: refinement steps
     of the adjoint solve in the backward calls.  dot: float32 dot-product
-    accumulation, 0 float pairs (default), 1 float64."""
+    accumulation, 0 float pairs (default), 1 float64.  refine_tol: exit
+    tolerance of refinement's correction solves (<= 0: tol)."""
     o = L.mpcg_opts(float(tol), int(tol_mode), int(max_iter), int(cluster), int(mode), None, 0,
-                    int(precon), int(refine), int(dot))
+                    int(precon), int(refine), int(dot), float(refine_tol))
     if instances is not None:  # a device int32 tensor of instance indices
         o.instances = instances.data_ptr()
         o.n_instances = int(instances.numel())

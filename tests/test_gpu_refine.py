@@ -104,3 +104,32 @@ def test_refinement_batched():
         assert oracle.relerr(lam[ko[b]:ko[b + 1]], lo) < 1e-6
         z = np.concatenate([dx[ko[b]:ko[b + 1]].ravel(), du[co[b]:co[b + 1]].ravel()])
         assert oracle.relerr(z, np.concatenate([xo.ravel(), uo.ravel()])) < TOL_F32
+
+
+def test_loose_correction_tolerance_reaches_the_same_accuracy():
+    """opts.refine_tol: the correction solve of a refinement step stops at its
+    own relative residual 1e-3 instead of the solve's 1e-6 -- the correction
+    only shrinks an error already at the float32 floor of S+ -- and lands
+    at the same accuracy in fewer iterations (nx = 36, N = 256)."""
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    s = solver()
+    N = 256
+    lq = gen.kuka_lq(36, 12, N, LARGE["seed_base"] + N, dt=LARGE["dt"], qd=LARGE["qd"]).astype(np.float32)
+    lo, _, _ = oracle_solution(lq)
+    lt = LQTensors.from_numpy(lq)
+    sch = s.alloc_schur(lt)
+    s.form(lt, sch)
+    lam0 = torch.zeros(N, 36, device="cuda")
+    s.pcg_solve(lt, sch, lam0, make_opts())
+    out = {}
+    for rt in (0.0, 1e-3):
+        lam = lam0.clone()
+        st = s.refine_step(lt, sch, lam, make_opts(refine_tol=rt))
+        torch.cuda.synchronize()
+        out[rt] = (oracle.relerr(lam.cpu().double().numpy(), lo), int(read_stats(st)["iters"][0]),
+                   int(read_stats(st)["status"][0]))
+    print(out)
+    assert out[0.0][2] == 0 and out[1e-3][2] == 0
+    assert out[0.0][0] < 1e-5 and out[1e-3][0] < 1e-5, out
+    assert out[1e-3][1] < 0.8 * out[0.0][1], out
