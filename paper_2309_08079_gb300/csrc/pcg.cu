@@ -596,6 +596,22 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
                     push_halo(hA_l, mbA_l, hA_r, mbA_r, up);
                     s1 = exchangeA(s1);
                     iters = it;
+                    // the boundary slots' halo operands do not depend on alpha:
+                    // load them before it is formed (one side per thread; a
+                    // thread owning both, when a CTA has one knot slot, loads
+                    // its right side late)
+                    T hh[RPT], hv[RPT];
+                    const bool hleft = kl == 0 && has_left, hright = kl == KPC - 1 && has_right;
+                    const int hbase = hleft ? 0 : (KPC + 1) * vs, hoff = hleft ? 0 : vs;
+                    const bool hboth = hleft && hright;
+#pragma unroll
+                    for (int m = 0; m < RPT; ++m) {
+                        hh[m] = hv[m] = T(0);
+                        if ((hleft || hright) && rows[m] < nx) {
+                            hh[m] = haloA[hoff + rows[m]];
+                            hv[m] = vecR[hbase + rows[m]];
+                        }
+                    }
                     if (timed_out) {
                         status = MPCG_TIMEOUT;
                         break;
@@ -613,10 +629,10 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
                         r_r[m] = fma_rn(-alpha, up[m], r_r[m]);
                         if (rx[m]) vecR[(kl + 1) * vs + rows[m]] = r_r[m];
                     }
-                    if (kl == 0 && has_left)
+                    if (hleft || hright)
                         for (int m = 0; m < RPT; ++m)
-                            if (rows[m] < nx) vecR[rows[m]] = fma_rn(-alpha, haloA[rows[m]], vecR[rows[m]]);
-                    if (kl == KPC - 1 && has_right)
+                            if (rows[m] < nx) vecR[hbase + rows[m]] = fma_rn(-alpha, hh[m], hv[m]);
+                    if (hboth)
                         for (int m = 0; m < RPT; ++m)
                             if (rows[m] < nx) {
                                 T *x = &vecR[(KPC + 1) * vs + rows[m]];
@@ -638,6 +654,15 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
                         status = MPCG_TIMEOUT;
                         break;
                     }
+                    // halo operands of the p update, loaded before beta is formed
+#pragma unroll
+                    for (int m = 0; m < RPT; ++m) {
+                        hh[m] = hv[m] = T(0);
+                        if ((hleft || hright) && rows[m] < nx) {
+                            hh[m] = haloB[hoff + rows[m]];
+                            hv[m] = vecP[hbase + rows[m]];
+                        }
+                    }
                     const T etan = AT::to_T(s2.eta);
                     rr_t = (T)s2.rr;
                     eta = s2.eta;
@@ -657,10 +682,10 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
                         p_r[m] = fma_rn(beta, p_r[m], rt[m]);
                         if (rx[m]) vecP[(kl + 1) * vs + rows[m]] = p_r[m];
                     }
-                    if (kl == 0 && has_left)
+                    if (hleft || hright)
                         for (int m = 0; m < RPT; ++m)
-                            if (rows[m] < nx) vecP[rows[m]] = fma_rn(beta, vecP[rows[m]], haloB[rows[m]]);
-                    if (kl == KPC - 1 && has_right)
+                            if (rows[m] < nx) vecP[hbase + rows[m]] = fma_rn(beta, hv[m], hh[m]);
+                    if (hboth)
                         for (int m = 0; m < RPT; ++m)
                             if (rows[m] < nx) {
                                 T *x = &vecP[(KPC + 1) * vs + rows[m]];
