@@ -68,8 +68,9 @@ __device__ __forceinline__ double rr_acc(float r, double acc) { return __fma_rn(
 __device__ __forceinline__ double rr_acc(double r, double acc) { return __fma_rn(r, r, acc); }
 
 // Shared-memory carve-up (dynamic).  Slot arrays hold one partial per
-// (source CTA, source warp).  Offsets in bytes, computed identically
-// on the host (pcg_smem_bytes) and the device.  A: accumulator type.
+// source CTA, the wpart arrays one per warp of this CTA.  Offsets in bytes,
+// computed identically on the host (pcg_smem_bytes) and the device.
+// A: accumulator type.
 template <typename T, typename A>
 struct SmemLayout {
     size_t vecP, vecR, haloA, haloB, slotA, slotB, wpartA, wpartB, mbar, misc, mats, total;
