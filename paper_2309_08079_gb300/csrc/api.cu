@@ -531,6 +531,7 @@ size_t mpcg_workspace_bytes(mpcg_dims d, int B) {
 
 int mpcg_form_schur_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,
                             const mpcg_lq *lq, mpcg_schur *s, void *stream) {
+    MPCG_NVTX("mpcg_form_schur_batched");
     if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !s->Sd ||
         (!s->So && d.N > 1) || !s->gamma)
         return MPCG_EINVAL;
@@ -543,6 +544,7 @@ int mpcg_form_schur(mpcg_handle *h, mpcg_dims d, const mpcg_lq *lq, mpcg_schur *
 
 int mpcg_form_schur_precon_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,
                                    const mpcg_lq *lq, mpcg_schur *s, void *stream) {
+    MPCG_NVTX("mpcg_form_schur_precon_batched");
     if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !s->Sd ||
         !s->Pd || !s->gamma || (d.N > 1 && (!s->So || !s->Po)))
         return MPCG_EINVAL;
@@ -556,6 +558,7 @@ int mpcg_form_schur_precon(mpcg_handle *h, mpcg_dims d, const mpcg_lq *lq, mpcg_
 
 int mpcg_form_precon_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off, mpcg_schur *s,
                              void *stream) {
+    MPCG_NVTX("mpcg_form_precon_batched");
     if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !s || !s->Sd || !s->Pd ||
         (d.N > 1 && (!s->So || !s->Po)))
         return MPCG_EINVAL;
@@ -569,6 +572,7 @@ int mpcg_form_precon(mpcg_handle *h, mpcg_dims d, mpcg_schur *s, void *stream) {
 int mpcg_pcg_solve_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,
                            const mpcg_schur *s, void *lambda, const mpcg_opts *opts,
                            mpcg_stats *stats, void *workspace, void *stream) {
+    MPCG_NVTX("mpcg_pcg_solve_batched");
     if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !s || !s->Sd || !s->Pd ||
         (d.N > 1 && (!s->So || !s->Po)) || !s->gamma || !lambda)
         return MPCG_EINVAL;
@@ -597,6 +601,7 @@ int mpcg_pcg_solve(mpcg_handle *h, mpcg_dims d, const mpcg_schur *s, void *lambd
 int mpcg_recover_step_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_off,
                               const mpcg_lq *lq, const void *lambda, void *dx, void *du,
                               void *stream) {
+    MPCG_NVTX("mpcg_recover_step_batched");
     if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !lambda || !dx ||
         (!du && d.N > 1))
         return MPCG_EINVAL;
@@ -612,6 +617,7 @@ int mpcg_refine_step_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot
                              const mpcg_lq *lq, const mpcg_schur *s, void *lambda,
                              const mpcg_opts *opts, mpcg_stats *stats, void *workspace,
                              void *stream) {
+    MPCG_NVTX("mpcg_refine_step_batched");
     if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !s->Sd ||
         !s->Pd || (d.N > 1 && (!s->So || !s->Po)) || !lambda || !workspace)
         return MPCG_EINVAL;
@@ -634,6 +640,7 @@ int mpcg_backward_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_of
                           const void *dx, const void *du, const void *lam_bar, const void *dx_bar,
                           const void *du_bar, const mpcg_grads *g, const mpcg_opts *opts,
                           mpcg_stats *stats, void *workspace, void *stream) {
+    MPCG_NVTX("mpcg_backward_batched");
     if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !lambda || !dx ||
         !lam_bar || !dx_bar || !g || !g->A || !g->B || !g->Qd || !g->Rd || !g->q || !g->r ||
         !g->c || !workspace || (d.N > 1 && (!du || !du_bar)) || (opts && opts->refine < 0))
@@ -708,6 +715,7 @@ extern "C" int mpcg_backward_batched_noalloc(mpcg_handle *h, mpcg_dims d, int B,
                                              const void *du_bar, const mpcg_grads *g,
                                              const mpcg_opts *opts, mpcg_stats *stats,
                                              void *stream) {
+    MPCG_NVTX("mpcg_backward_batched_noalloc");
     if (!h || !dims_ok(d) || B < 1 || (B > 1 && !knot_off) || !lq_ok(lq, d) || !s || !lambda || !dx ||
         !lam_bar || !dx_bar || !g || !g->A || !g->B || !g->Qd || !g->Rd || !g->q || !g->r ||
         !g->c || (d.N > 1 && (!du || !du_bar)) || (opts && opts->refine < 0))

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/mpcg.h"
@@ -415,5 +416,16 @@ struct BatchView {
 };
 
 __host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// An NVTX range over a host call (visible to Nsight and other NVTX tools; a
+// no-op when none is attached).  The C ABI's entry points open one each.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define MPCG_NVTX(name) ::mpcg::NvtxRange mpcg_nvtx_range_(name)
+
 
 }  // namespace mpcg

@@ -350,6 +350,7 @@ int mpcg_linearize_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot_o
                            const mpcg_model *model, const void *X, const void *U,
                            const void *xref, const void *xs, const mpcg_lq_out *out,
                            void *stream) {
+    MPCG_NVTX("mpcg_linearize_batched");
     if (!h || B < 1 || (B > 1 && !knot_off) || !model_ok(model, d) || !X || !xref || !xs || !out ||
         !out->Qd || !out->q || !out->c ||
         (d.N > 1 && (!U || !out->A || !out->B || !out->Rd || !out->r)))
@@ -370,6 +371,7 @@ int mpcg_line_search_batched(mpcg_handle *h, mpcg_dims d, int B, const int *knot
                              const void *dU, const void *xref, const void *xs,
                              const void *lambda, double mu, int n_alpha, double *merit,
                              int *alpha_index, void *stream) {
+    MPCG_NVTX("mpcg_line_search_batched");
     if (!h || B < 1 || (B > 1 && !knot_off) || !model_ok(model, d) || !X || !dX || !xref || !xs ||
         !merit || n_alpha < 1 || n_alpha > MAX_ALPHA || (d.N > 1 && (!U || !dU)) ||
         (!(mu > 0.0) && !lambda))
