@@ -570,11 +570,25 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
             --outstanding;
         };
         // one pass: kind 0 = residual out = b - S v (dot += b^2); kind 1 =
-        // product out = M v with partial dots (v . out, v . v)
-        auto run_pass = [&](int kind, int ps, const T *v, T *out, A &dot, T &sq) {
+        // product out = M v with partial dots (v . out, v . v).  lam_alpha
+        // != 0: each step also applies lambda += lam_alpha p to its knot's
+        // rows (p is not written during a pass), with the global loads issued
+        // before the step's tile wait, so their latency hides behind it.
+        auto run_pass = [&](int kind, int ps, const T *v, T *out, A &dot, T &sq, T lam_alpha = T(0)) {
             const T *Mo = (ps & 1) ? P.Po : P.So;
+            const bool lam_upd = lam_alpha != T(0);
             for (int t = 0; t < Lmax; ++t) {
                 const bool act = t < len;
+                T lv[RPT];
+                T *lrow = nullptr;
+                if (lam_upd && act) {
+                    lrow = P.lam + (size_t)(k0 + ks0 + t) * nx;
+#pragma unroll
+                    for (int m = 0; m < RPT; ++m) {
+                        const int i = li + m * LPK;
+                        lv[m] = i < nx ? lrow[i] : T(0);
+                    }
+                }
                 __syncwarp();
                 if (act) {
                     if (leader) {
@@ -619,6 +633,7 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
                                 const T vi = v[o];
                                 dot = AT::add(dot, AT::prod(vi, y[m]));
                                 sq = fma_rn(vi, vi, sq);
+                                if (lam_upd) lrow[i] = fma_rn(lam_alpha, vp[o], lv[m]);
                             }
                         }
                     }
@@ -695,32 +710,17 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
                         break;
                     }
                     const T alpha = AT::div(eta_t, ups);
-                    // lambda += alpha p in global memory: each thread's four
-                    // loads are issued before any store, so their latencies
-                    // overlap
-                    T *lam0 = P.lam + (size_t)k0 * nx;
-                    const int nel = Nb * nx;
-                    for (int e0 = tid; e0 < nel; e0 += 4 * nthreads) {
-                        T l[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int e = e0 + u * nthreads;
-                            l[u] = e < nel ? lam0[e] : T(0);
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int e = e0 + u * nthreads;
-                            if (e < nel) {
-                                const int o = (e / nx + 1) * vs + e % nx;
-                                lam0[e] = fma_rn(alpha, vp[o], l[u]);
-                                vr[o] = fma_rn(-alpha, vw[o], vr[o]);
-                            }
-                        }
+                    // r -= alpha S p (shared memory); lambda += alpha p rides
+                    // on the next pass, step by step
+                    for (int e = tid; e < Nb * nx; e += nthreads) {
+                        const int o = (e / nx + 1) * vs + e % nx;
+                        vr[o] = fma_rn(-alpha, vw[o], vr[o]);
                     }
                     __syncthreads();
                     A s2 = AT::zero();
                     T sq2 = T(0);
-                    run_pass(1, ps++, vr, vw, s2, sq2);  // r~ = Phi^-1 r, r^T r~, ||r||^2
+                    // r~ = Phi^-1 r, r^T r~, ||r||^2; lambda += alpha p
+                    run_pass(1, ps++, vr, vw, s2, sq2, alpha);
                     A s2b = AT::prod(sq2, T(1));
                     reduce2(s2, s2b);
                     if (__syncthreads_or(failed)) {
