@@ -291,6 +291,11 @@ struct TileLayout {
         w = o; o = al(o + v);
         tile_bytes = (sizeof(T) * (size_t)nx * nx + 15) & ~size_t(15);
         stream_bytes = (size_t)tile_slots(depth) * tile_bytes;
+        // Two 16-lane streams share a warp when nx <= 16; their rings are
+        // padded to 64 bytes past a multiple of 128, so the two half-warps'
+        // column reads of their upper blocks (14 consecutive words each,
+        // same slot offset) fall on disjoint banks.
+        if (nx <= 16) stream_bytes += (64 + 128 - stream_bytes % 128) % 128;
         tiles = o; o = al(o + (size_t)NS * stream_bytes);
         mbar = o; o = al(o + (size_t)NS * (depth + 1) * sizeof(uint64_t));
         wpart = o; o = al(o + 2 * sizeof(A) * W);
