@@ -275,6 +275,35 @@ def test_stair_precon_iterates_match_the_oracle(nx, nu, dtype, mode):
 
 
 @pytest.mark.parametrize("mode", [1, 2, 3])
+@pytest.mark.parametrize("nx,nu,dtype", [(14, 7, "float32"), (14, 7, "float64"), (36, 12, "float32")])
+def test_capped_iterate_matches_the_oracle(nx, nu, dtype, mode):
+    """With the default symmetric stair Phi^-1 and a fixed iteration count,
+    every kernel form returns Algorithm 1's iterate after exactly that many
+    iterations (the oracle's pcg on the same rounded inputs, warm-started
+    from the same lambda0): lambda += alpha p is applied once per iteration,
+    whether it runs as its own loop or rides on the next product pass, and
+    the solve reports NOT_CONVERGED.  An iterate one step off differs by
+    ~10 % at this count."""
+    from paper_2309_08079_gb300.solver import make_opts
+    f32 = dtype == "float32"
+    m = 9
+    N = 48
+    lq_in = gen.kuka_lq(nx, nu, N, 940 + nx).astype(np.float32 if f32 else np.float64)
+    Sd, So, g = oracle.schur_blocks(lq_in.astype(np.float64))
+    Pd, Po = oracle.precon_blocks(Sd, So)
+    lam0 = gen.warm_start(oracle.kkt_solve(lq_in.astype(np.float64))[0], 940, 0, rel=0.3)
+    lam0 = lam0.astype(np.float32 if f32 else np.float64)
+    lo, it, _ = oracle.pcg(Sd, So, Pd, Po, -g, lam0=lam0, tol=1e-30, max_iter=m)
+    assert it == m
+    lo_prev, _, _ = oracle.pcg(Sd, So, Pd, Po, -g, lam0=lam0, tol=1e-30, max_iter=m - 1)
+    assert oracle.relerr(lo_prev, lo) > 1e-2  # the check below resolves one iteration
+    lam, _, _, st, _ = run_gpu(lq_in, dtype, lam0=lam0, opts=make_opts(mode=mode, tol=1e-30, max_iter=m))
+    assert st["status"][0] == 1 and st["iters"][0] == m, st
+    e = oracle.relerr(lam, lo.reshape(lam.shape))
+    assert e < (1e-3 if f32 else 1e-9), e
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
 def test_stair_precon_parity_in_a_ragged_batch(mode):
     """The row mask follows each instance's own knot index in a batch
     (instances of odd and even lengths back to back)."""
