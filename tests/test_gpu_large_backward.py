@@ -18,14 +18,14 @@ LARGE = gen.CONFIG_LARGE
 GRAD_BAR = 1e-4
 
 
-def _grads(lt, w, refine, workspace=None):
+def _grads(lt, w, refine, workspace=None, refine_tol=0.0):
     import torch
     from paper_2309_08079_gb300.autograd import MPCGSolve
     from paper_2309_08079_gb300.solver import make_opts
     s = solver()
     leaves = {f: getattr(lt, f).clone().requires_grad_(True) for f in FIELDS}
     cfg = dict(solver=s, nx=lt.nx, nu=lt.nu, N=lt.N, knot_off=lt.knot_off, nb=lt.nb,
-               total=lt.total, opts=make_opts(), refine=refine,
+               total=lt.total, opts=make_opts(refine_tol=refine_tol), refine=refine,
                workspace=workspace if workspace is not None else s.alloc_workspace(lt))
     lam, dx, du, _ = MPCGSolve.apply(*(leaves[f] for f in FIELDS), None, cfg)
     wt = torch.as_tensor(w, dtype=torch.float32, device="cuda")
@@ -58,16 +58,19 @@ def test_large_state_backward_meets_the_oracle(N):
     assert max(e1.values()) < max(e0.values()), (e0, e1)
 
 
-def test_large_state_backward_batched():
+@pytest.mark.parametrize("refine_tol", [0.0, 1e-2])
+def test_large_state_backward_batched(refine_tol):
     """A ragged batch of large-state instances through the batched backward
-    with refinement: every instance's gradient, field by field."""
+    with refinement: every instance's gradient, field by field.  Also with
+    the refinement's correction solves stopped at relative residual 1e-2
+    (the large-state workload's setting), for the forward and the adjoint."""
     from paper_2309_08079_gb300.solver import LQTensors
     Ns = [64, 150, 256, 97]
     batch = gen.kuka_batch(36, 12, Ns, LARGE["seed_base"], dt=LARGE["dt"], qd=LARGE["qd"]).astype(np.float32)
     K = int(batch.knot_off[-1])
     w = gen.loss_weights(K * 36, LARGE["seed_base"]).reshape(K, 36)
     lt = LQTensors.from_batch(batch)
-    g = _grads(lt, w, refine=1)
+    g = _grads(lt, w, refine=1, refine_tol=refine_tol)
     ko, co = batch.knot_off, batch.ctrl_off()
     for b, it in enumerate(batch.items):
         e = _field_errs(g, _oracle_grad(it, w[ko[b]:ko[b + 1]]), slice(ko[b], ko[b + 1]),

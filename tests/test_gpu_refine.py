@@ -110,7 +110,8 @@ def test_loose_correction_tolerance_reaches_the_same_accuracy():
     """opts.refine_tol: the correction solve of a refinement step stops at its
     own relative residual 1e-3 instead of the solve's 1e-6 -- the correction
     only shrinks an error already at the float32 floor of S+ -- and lands
-    at the same accuracy in fewer iterations (nx = 36, N = 256)."""
+    at the same accuracy in fewer iterations (nx = 36, N = 256); at 1e-2
+    it stays within a quarter of the 1e-4 bar in fewer still."""
     import torch
     from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
     s = solver()
@@ -123,13 +124,13 @@ def test_loose_correction_tolerance_reaches_the_same_accuracy():
     lam0 = torch.zeros(N, 36, device="cuda")
     s.pcg_solve(lt, sch, lam0, make_opts())
     out = {}
-    for rt in (0.0, 1e-3):
+    for rt in (0.0, 1e-3, 1e-2):
         lam = lam0.clone()
         st = s.refine_step(lt, sch, lam, make_opts(refine_tol=rt))
         torch.cuda.synchronize()
         out[rt] = (oracle.relerr(lam.cpu().double().numpy(), lo), int(read_stats(st)["iters"][0]),
                    int(read_stats(st)["status"][0]))
     print(out)
-    assert out[0.0][2] == 0 and out[1e-3][2] == 0
-    assert out[0.0][0] < 1e-5 and out[1e-3][0] < 1e-5, out
-    assert out[1e-3][1] < 0.8 * out[0.0][1], out
+    assert out[0.0][2] == 0 and out[1e-3][2] == 0 and out[1e-2][2] == 0
+    assert out[0.0][0] < 1e-5 and out[1e-3][0] < 1e-5 and out[1e-2][0] < 2.5e-5, out
+    assert out[1e-2][1] < out[1e-3][1] < 0.8 * out[0.0][1], out
