@@ -74,7 +74,7 @@ extern "C" {
 #define MPCG_BREAKDOWN 2     /* p^T S+ p <= 0 or not finite */
 #define MPCG_NONFINITE 3     /* a residual or preconditioned residual is not finite */
 #define MPCG_BADINPUT 4      /* form_schur found Qd or Rd <= 0 or not finite */
-#define MPCG_TIMEOUT 5       /* a bounded device wait gave up (never expected) */
+#define MPCG_TIMEOUT 5       /* a bounded device wait gave up (never expected); lambda is then unspecified */
 
 /* info bits written by mpcg_form_schur into mpcg_schur.info[b] */
 #define MPCG_INFO_BADINPUT 1u
