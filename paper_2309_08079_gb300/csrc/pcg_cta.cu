@@ -264,8 +264,10 @@ __global__ void __launch_bounds__(512, 1) pcg_cta_kernel(const PcgParams<T> P) {
 // pass (a pass is one product with S+ or with Phi^-1).  A step of a stream
 // consumes the tiles of one knot k: the diagonal block D_k and the
 // off-diagonal block O_k = block (k+1, k), which serves as the upper block of
-// row k (read by columns) and, one step later, as the lower block of row k+1
-// (read by rows), so each block crosses HBM once per pass.  The tiles
+// row k (read by columns) and, in the same step, as the lower block of row
+// k+1 (read by rows; the products, which need only v_k, are carried in
+// registers to the next step), so each block crosses HBM once per pass and
+// leaves its ring slot after one step.  The tiles
 // arrive by TMA bulk copies that complete on the stream's own mbarriers;
 // the copies for step g+1 are issued when step g starts, across pass
 // boundaries, so a stream's memory traffic keeps flowing while the CTA forms
@@ -275,8 +277,8 @@ __global__ void __launch_bounds__(512, 1) pcg_cta_kernel(const PcgParams<T> P) {
 // order, as reading its column i.
 // ---------------------------------------------------------------------------
 // Per knot stream and pipeline depth d: a ring of d+1 diagonal-block tiles,
-// d+2 off-diagonal tiles and d+1 mbarriers.
-__host__ __device__ constexpr int tile_slots(int depth) { return 2 * depth + 3; }
+// d+1 off-diagonal tiles and d+1 mbarriers.
+__host__ __device__ constexpr int tile_slots(int depth) { return 2 * depth + 2; }
 
 template <typename T>
 struct TileLayout {
@@ -320,20 +322,20 @@ __device__ __forceinline__ void vload(const T *p, T (&o)[VW]) {
     }
 }
 
-// Rows li, li + LPK, ... (RPT of them; rows >= nx skipped) of one block row
-// of the tiles times the halo'd vector: D (by rows), the lower block from a
-// tile (Lt, by rows; nullptr: none or Lg), the upper block U (by columns;
-// nullptr: none).  One pass over the columns feeds six accumulators (per
-// block, even and odd columns apart), so six dependency chains of nx / 2
-// products overlap; each adds its products in column order.  nx % VW == 0.
-template <typename T, int VW, int RPT, int LPK, bool HL, bool HU>
+// One column group [j, j + VW) of rows li, li + LPK, ... (RPT of them; rows
+// >= nx skipped) of block row k: D_k by rows times v_k and, with HU, the
+// upper block O_k = block (k+1, k) by columns times v_{k+1}; with HN also
+// O_k by rows times v_k -- the lower-block products of row k+1, which the
+// stream's next step uses while O_k's slot is already being refilled.  Each
+// block's products go to two accumulators (even and odd columns), each in
+// column order.  nx % VW == 0.
+template <typename T, int VW, int RPT, int LPK, bool HU, bool HN>
 __device__ __forceinline__ void tile_cols(int nx, int j, int li, const bool (&ok)[RPT], const T *D,
-                                          const T *Lt, const T *U, const T *vprev, const T *vself,
-                                          const T *vnext, T (&a0)[RPT], T (&a1)[RPT], T (&a2)[RPT],
-                                          T (&b0)[RPT], T (&b1)[RPT], T (&b2)[RPT]) {
-    T xs[VW], xp[VW], xn[VW];
+                                          const T *O, const T *vself, const T *vnext, T (&a0)[RPT],
+                                          T (&a2)[RPT], T (&b0)[RPT], T (&b2)[RPT], T (&c1)[RPT],
+                                          T (&d1)[RPT]) {
+    T xs[VW], xn[VW];
     vload<T, VW>(vself + j, xs);
-    if (HL) vload<T, VW>(vprev + j, xp);
     if (HU) vload<T, VW>(vnext + j, xn);
 #pragma unroll
     for (int m = 0; m < RPT; ++m)
@@ -341,30 +343,33 @@ __device__ __forceinline__ void tile_cols(int nx, int j, int li, const bool (&ok
             const int i = li + m * LPK;
             T d[VW], l[VW];
             vload<T, VW>(D + i * nx + j, d);
-            if (HL) vload<T, VW>(Lt + i * nx + j, l);
+            if (HN) vload<T, VW>(O + i * nx + j, l);
 #pragma unroll
-            for (int t = 0; t < VW; t += 2) {  // even columns into a, odd into b
+            for (int t = 0; t < VW; t += 2) {  // even columns into a / c, odd into b / d
                 a0[m] = fma_rn(d[t], xs[t], a0[m]);
-                if (HL) a1[m] = fma_rn(l[t], xp[t], a1[m]);
-                if (HU) a2[m] = fma_rn(U[(j + t) * nx + i], xn[t], a2[m]);
+                if (HN) c1[m] = fma_rn(l[t], xs[t], c1[m]);
+                if (HU) a2[m] = fma_rn(O[(j + t) * nx + i], xn[t], a2[m]);
                 b0[m] = fma_rn(d[t + 1], xs[t + 1], b0[m]);
-                if (HL) b1[m] = fma_rn(l[t + 1], xp[t + 1], b1[m]);
-                if (HU) b2[m] = fma_rn(U[(j + t + 1) * nx + i], xn[t + 1], b2[m]);
+                if (HN) d1[m] = fma_rn(l[t + 1], xs[t + 1], d1[m]);
+                if (HU) b2[m] = fma_rn(O[(j + t + 1) * nx + i], xn[t + 1], b2[m]);
             }
         }
 }
 
-// Rows li, li + LPK, ... (RPT of them; rows >= nx skipped) of one block row
-// of the tiles times the halo'd vector: D (by rows), the lower block from a
-// tile (Lt, by rows; nullptr: none or Lg), the upper block U (by columns;
-// nullptr: none).  One pass over the columns feeds six accumulators (per
-// block, even and odd columns apart: half the chain depth, measured 1-2 %
-// faster), summed as ((D_e + D_o) + (L_e + L_o)) + (U_e + U_o).  nx % VW == 0.  NXC > 0
+// Rows li, li + LPK, ... (RPT of them; rows >= nx skipped) of block row k
+// times the halo'd vector.  The lower block's products come from the
+// previous step of the stream (lc: carried in cl / dl, and ts for the split
+// rows), or, on a stream's first knot, from Lg (O_{k-1} straight from global
+// memory, sequential columns); the diagonal and the upper block (hu) are
+// swept here, and with hn the carry for row k+1 is formed from O_k (out in
+// cl / dl / ts).  Sum: ((D_e + D_o) + (L_e + L_o)) + (U_e + U_o), the even
+// / odd column split halving the chains (measured 1-2 % faster).  NXC > 0
 // fixes nx at compile time (the column loop unrolls completely).
 template <typename T, int VW, int RPT, int LPK, int NXC>
-__device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T *Lt, const T *Lg,
-                                          const T *U, const T *vprev, const T *vself,
-                                          const T *vnext, T (&y)[RPT]) {
+__device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T *O, bool hu, bool hn,
+                                          const T *Lg, bool lc, const T *vprev, const T *vself,
+                                          const T *vnext, T (&y)[RPT], T (&cl)[RPT], T (&dl)[RPT],
+                                          T &ts) {
     const int nx = NXC > 0 ? NXC : nx_rt;
     // nx fixed a little above a warp (nx = 36): the 4 rows past the first 32
     // are split over the whole warp, 8 lanes per row with a strided subset
@@ -372,32 +377,32 @@ __device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T
     // pass in which 4 of 32 lanes work.  (These rows keep their own, equally
     // valid, summation order.)
     constexpr bool SPLIT = RPT == 2 && LPK == 32 && NXC > LPK && NXC - LPK <= 4;
-    T a0[RPT], a1[RPT], a2[RPT], b0[RPT], b1[RPT], b2[RPT];
+    T a0[RPT], a1[RPT], a2[RPT], b0[RPT], b1[RPT], b2[RPT], c1[RPT], d1[RPT];
     bool ok[RPT];
 #pragma unroll
     for (int m = 0; m < RPT; ++m) {
-        a0[m] = a1[m] = a2[m] = b0[m] = b1[m] = b2[m] = T(0);
+        a0[m] = a2[m] = b0[m] = b2[m] = c1[m] = d1[m] = T(0);
+        a1[m] = lc ? cl[m] : T(0);
+        b1[m] = lc ? dl[m] : T(0);
         ok[m] = li + m * LPK < nx && !(SPLIT && m > 0);
     }
-    auto sweep = [&](auto hl, auto hu) {
-        constexpr bool HL = decltype(hl)::value, HU = decltype(hu)::value;
+    auto sweep = [&](auto u_, auto n_) {
+        constexpr bool HU = decltype(u_)::value, HN = decltype(n_)::value;
         if constexpr (NXC > 0) {
 #pragma unroll
             for (int j = 0; j < NXC; j += VW)
-                tile_cols<T, VW, RPT, LPK, HL, HU>(nx, j, li, ok, D, Lt, U, vprev, vself, vnext, a0, a1, a2,
-                                                   b0, b1, b2);
+                tile_cols<T, VW, RPT, LPK, HU, HN>(nx, j, li, ok, D, O, vself, vnext, a0, a2, b0, b2, c1, d1);
         } else {
 #pragma unroll 2
             for (int j = 0; j < nx; j += VW)
-                tile_cols<T, VW, RPT, LPK, HL, HU>(nx, j, li, ok, D, Lt, U, vprev, vself, vnext, a0, a1, a2,
-                                                   b0, b1, b2);
+                tile_cols<T, VW, RPT, LPK, HU, HN>(nx, j, li, ok, D, O, vself, vnext, a0, a2, b0, b2, c1, d1);
         }
     };
     using Y = std::true_type;
     using N = std::false_type;
-    if (Lt && U) sweep(Y{}, Y{});
-    else if (Lt) sweep(Y{}, N{});
-    else if (U) sweep(N{}, Y{});
+    if (hu && hn) sweep(Y{}, Y{});
+    else if (hu) sweep(Y{}, N{});
+    else if (hn) sweep(N{}, Y{});
     else sweep(N{}, N{});
     if (Lg) {  // lower block of a stream's first knot, straight from global memory
 #pragma unroll
@@ -407,21 +412,26 @@ __device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T
                     a1[m] = fma_rn(__ldg(Lg + (li + m * LPK) * nx + j), vprev[j], a1[m]);
     }
 #pragma unroll
-    for (int m = 0; m < RPT; ++m) y[m] = ((a0[m] + b0[m]) + (a1[m] + b1[m])) + (a2[m] + b2[m]);
+    for (int m = 0; m < RPT; ++m) {
+        y[m] = ((a0[m] + b0[m]) + (a1[m] + b1[m])) + (a2[m] + b2[m]);
+        cl[m] = c1[m];
+        dl[m] = d1[m];
+    }
     if constexpr (SPLIT) {
         const int row = LPK + (li >> 3), g = li & 7;
         const bool live = row < NXC;
-        const T *Ls = Lt ? Lt : Lg;  // tile (shared) or global: generic loads
-        T t0 = T(0), t1 = T(0), t2 = T(0);
+        T t0 = T(0), t1 = lc ? ts : T(0), t2 = T(0), tn = T(0);
 #pragma unroll
         for (int q = 0; q < (NXC + 7) / 8; ++q) {
             const int j = g + 8 * q;
             if (live && j < NXC) {
                 t0 = fma_rn(D[row * NXC + j], vself[j], t0);
-                if (Ls) t1 = fma_rn(Ls[row * NXC + j], vprev[j], t1);
-                if (U) t2 = fma_rn(U[j * NXC + row], vnext[j], t2);
+                if (Lg) t1 = fma_rn(Lg[row * NXC + j], vprev[j], t1);
+                if (hu) t2 = fma_rn(O[j * NXC + row], vnext[j], t2);
+                if (hn) tn = fma_rn(O[row * NXC + j], vself[j], tn);
             }
         }
+        ts = tn;
         T t = (t0 + t1) + t2;
         t += __shfl_xor_sync(0xffffffffu, t, 1);
         t += __shfl_xor_sync(0xffffffffu, t, 2);
@@ -432,15 +442,12 @@ __device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T
 
 // b_i - (row i) . v with exact products and an extended sum (as resid_ptr)
 template <typename T>
-__device__ __forceinline__ T tile_resid(int nx, int i, T b, const T *D, const T *Lt, const T *Lg,
-                                        const T *U, const T *vprev, const T *vself,
-                                        const T *vnext) {
+__device__ __forceinline__ T tile_resid(int nx, int i, T b, const T *D, const T *Lg, const T *U,
+                                        const T *vprev, const T *vself, const T *vnext) {
     using AT = Acc<T>;
     typename AT::type a = AT::prod(b, T(1));
     for (int j = 0; j < nx; ++j) a = AT::add(a, AT::prod(-D[i * nx + j], vself[j]));
-    if (Lt)
-        for (int j = 0; j < nx; ++j) a = AT::add(a, AT::prod(-Lt[i * nx + j], vprev[j]));
-    else if (Lg)
+    if (Lg)
         for (int j = 0; j < nx; ++j) a = AT::add(a, AT::prod(-__ldg(Lg + i * nx + j), vprev[j]));
     if (U)
         for (int j = 0; j < nx; ++j) a = AT::add(a, AT::prod(-U[j * nx + i], vnext[j]));
@@ -469,7 +476,7 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
     const int nx = NXC > 0 ? NXC : P.nx, vs = P.vs, nx2 = nx * nx;
     const uint32_t nxb = (uint32_t)(nx2 * sizeof(T));
     const int depth = P.depth;       // steps copied ahead
-    const int RD = depth + 1, RO = depth + 2, RM = depth + 1;  // ring sizes
+    const int RD = depth + 1, RO = depth + 1, RM = depth + 1;  // ring sizes
     TileLayout<T> Lo(P.kpc_max, vs, W, NS, nx, depth);
     T *vr = reinterpret_cast<T *>(smem + Lo.r);
     T *vp = reinterpret_cast<T *>(smem + Lo.p);
@@ -537,7 +544,6 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
         int i_t = 0, i_ps = 0;     // next step to issue: knot offset, pass
         int i_d = 0, i_o = 0, i_m = 0;  // its D slot, O slot, barrier
         int c_d = 0, c_o = 0, c_m = 0;  // next step to consume: D slot, O slot, barrier
-        int c_op = RO - 1;              // O slot of the step before it
         auto wrap = [](int x, int n) { return x + 1 == n ? 0 : x + 1; };
         auto tile = [&](int slot) { return reinterpret_cast<T *>(tb + (size_t)slot * Lo.tile_bytes); };
         // the copies of the next step to issue (leader lane; len > 0): even
@@ -574,7 +580,6 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
             return __any_sync(0xffffffffu, f) != 0;
         };
         auto advance_use = [&]() {
-            c_op = c_o;
             c_d = wrap(c_d, RD);
             c_o = wrap(c_o, RO);
             c_m = wrap(c_m, RM);
@@ -588,6 +593,12 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
         auto run_pass = [&](int kind, int ps, const T *v, T *out, A &dot, T &sq, T lam_alpha = T(0)) {
             const T *Mo = (ps & 1) ? P.Po : P.So;
             const bool lam_upd = lam_alpha != T(0);
+            // row k uses its off-diagonal blocks (all but the block Jacobi
+            // rows of a Phi^-1 pass, and the even rows of the stair's)
+            auto offd = [&](int k) { return !((ps & 1) && (P.precon == 1 || (P.precon == 2 && (k & 1) == 0))); };
+            T cl[RPT], dl[RPT], ts = T(0);  // lower-block products carried to the next step
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) cl[m] = dl[m] = T(0);
             for (int t = 0; t < Lmax; ++t) {
                 const bool act = t < len;
                 T lv[RPT];
@@ -614,27 +625,36 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
                 }
                 if (act) {
                     const int k = ks0 + t;
-                    const bool off = !((ps & 1) && (P.precon == 1 || (P.precon == 2 && (k & 1) == 0)));
+                    const bool off = offd(k);
                     const T *D = tile(c_d);
-                    const T *U = (off && k + 1 < Nb) ? tile(RD + c_o) : nullptr;
-                    const T *Lt = (off && k >= 1 && t >= 1) ? tile(RD + c_op) : nullptr;
-                    const T *Lg = (off && k >= 1 && t == 0) ? Mo + (size_t)(c0 + k - 1) * nx2 : nullptr;
+                    // O_k was copied when some row uses it (as in issue_next)
+                    const T *O = (k + 1 < Nb && !((ps & 1) && P.precon == 1)) ? tile(RD + c_o) : nullptr;
+                    const bool hu = off && k + 1 < Nb;
                     advance_use();
                     if (kind == 0) {
+                        // the residual pass (once per solve) reads every
+                        // lower block from global memory
+                        const T *Lg = (off && k >= 1) ? Mo + (size_t)(c0 + k - 1) * nx2 : nullptr;
 #pragma unroll
                         for (int m = 0; m < RPT; ++m) {
                             const int i = li + m * LPK;
                             if (i < nx) {
                                 const T bi = P.rhs_sign * P.rhs[(size_t)(k0 + k) * nx + i];
-                                out[(k + 1) * vs + i] = tile_resid<T>(nx, i, bi, D, Lt, Lg, U, v + k * vs,
+                                out[(k + 1) * vs + i] = tile_resid<T>(nx, i, bi, D, Lg, hu ? O : nullptr, v + k * vs,
                                                                       v + (k + 1) * vs, v + (k + 2) * vs);
                                 dot = AT::add(dot, AT::prod(bi, bi));
                             }
                         }
                     } else {
+                        // row k's lower products: carried from step t - 1, or
+                        // O_{k-1} from global memory on the range's first knot
+                        const bool lc = off && t >= 1;
+                        const T *Lg = (off && k >= 1 && t == 0) ? Mo + (size_t)(c0 + k - 1) * nx2 : nullptr;
+                        // row k+1's, for this stream's next step
+                        const bool hn = t + 1 < len && k + 1 < Nb && offd(k + 1);
                         T y[RPT];
-                        tile_rows<T, VW, RPT, LPK, NXC>(nx, li, D, Lt, Lg, U, v + k * vs, v + (k + 1) * vs,
-                                                   v + (k + 2) * vs, y);
+                        tile_rows<T, VW, RPT, LPK, NXC>(nx, li, D, O, hu, hn, Lg, lc, v + k * vs,
+                                                        v + (k + 1) * vs, v + (k + 2) * vs, y, cl, dl, ts);
 #pragma unroll
                         for (int m = 0; m < RPT; ++m) {
                             const int i = li + m * LPK;
