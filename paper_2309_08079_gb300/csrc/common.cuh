@@ -284,6 +284,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
     }
 }
 
+// As mbar_wait_bounded without the spin: try_wait from the start, so a
+// waiting warp leaves its issue slots to the SM's other warps (for kernels
+// whose warps stream independently rather than wait on one critical path).
+__device__ __forceinline__ bool mbar_wait_bounded_sleep(uint32_t mbar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
 // As mbar_wait_bounded, and also gives up once the word at shared address
 // `abort_flag` (this CTA's shared memory) is non-zero: a peer that has given
 // up sets it.  The flag is read only after the fast spin, so a healthy

@@ -573,9 +573,15 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
         // wait for the next step's tiles (leader polls; warp-uniform result)
         auto wait_next = [&](bool act) -> bool {
             int f = 0;
-            if (act && leader)
-                f = !mbar_wait_bounded(mbs + (uint32_t)(c_m * sizeof(uint64_t)), (ph >> c_m) & 1u,
-                                       WAIT_LIMIT_NS);
+            if (act && leader) {
+                // 16-lane streams (nx <= 16, up to 16 warps): a waiting warp
+                // sleeps and leaves its issue slots to the SM's other warps
+                // (measured 2 % faster); 32-lane streams (at most 2 warps
+                // per SMSP) spin, which wakes sooner (5 % faster at nx = 36)
+                const uint32_t bar = mbs + (uint32_t)(c_m * sizeof(uint64_t)), par = (ph >> c_m) & 1u;
+                f = LPK == 16 ? !mbar_wait_bounded_sleep(bar, par, WAIT_LIMIT_NS)
+                              : !mbar_wait_bounded(bar, par, WAIT_LIMIT_NS);
+            }
             if (act) ph ^= 1u << c_m;
             return __any_sync(0xffffffffu, f) != 0;
         };
