@@ -617,17 +617,22 @@ def run_batched(s, dev, solves):
     xcache = {}
 
     def cluster_floor_ms(groups, iters):
-        sm_ns, shapes = 0.0, []
+        """(floor over the cluster groups, their shapes, the instances of
+        the other groups, which stream their operators from HBM)."""
+        sm_ns, shapes, other = 0.0, [], []
         for o_g, N_g, idx in groups:
             sh = s.pcg_shape(lt, sch, o_g, N=N_g)
             if sh["form"] != "cluster":
-                return None, None  # a CTA-kernel group: no exchange floor
+                other.extend(int(i) for i in idx)
+                continue
             key = (sh["C"], sh["threads"] // 32)
             if key not in xcache:
                 xcache[key] = s.bench_exchange(*key, rounds=1000)["ns"]
             sm_ns += float(np.sum(iters[idx])) * 2.0 * xcache[key] * sh["C"]
             shapes.append({"C": sh["C"], "threads": sh["threads"], "instances": int(len(idx))})
-        return sm_ns / n_sms * 1e-6, shapes
+        if not shapes:
+            return None, None, other
+        return sm_ns / n_sms * 1e-6, shapes, other
 
     # capture the repeated solves in one graph, once per PCG kernel form
     per_mode = {}
@@ -666,15 +671,23 @@ def run_batched(s, dev, solves):
             it_b = stb["iters"].astype(np.float64).reshape(solves, batch.B).sum(axis=0)
             groups = ([(om, int(np.max(Ns)), np.arange(batch.B))] if name == "cluster" else
                       [(l.opts, l.N, l.inst.cpu().numpy()) for l in om.launches])
-            floor, shapes = cluster_floor_ms(groups, it_b)
+            floor, shapes, other = cluster_floor_ms(groups, it_b)
         else:
-            floor, shapes = None, None
+            floor, shapes, other = None, None, []
         if floor is not None:
             roof = {"bound": "sync_latency", "frac": floor / gms, "floor_ms": floor, "shapes": shapes,
-                    "note": "SM-time of every instance at 2 measured exchanges (mpcg_bench_exchange, its "
-                            "launch shape) per PCG iteration, spread over all SMs, over the graph time "
-                            "(formation and recovery included); operators stay on chip",
+                    "note": "SM-time of every cluster-launched instance at 2 measured exchanges "
+                            "(mpcg_bench_exchange, its launch shape) per PCG iteration, spread over all "
+                            "SMs, over the graph time (formation and recovery included); operators stay "
+                            "on chip",
                     "hbm_equivalent_frac": hbm_frac, "peak_source": note}
+            if other:
+                # a mixed plan: the tiled (or L2) groups stream their operators
+                ot = np.asarray(other)
+                alg_o = float(np.sum(it_b[ot] * Ns[ot])) * pcg_bytes_per_knot_iter(c["nx"])
+                roof["other_groups"] = {"instances": int(len(ot)), "bound": "hbm",
+                                        "frac": alg_o / (gms / 1e3) / 1e9 / hbm,
+                                        "note": "their PCG algorithmic bytes over the same graph time"}
         else:
             roof = {"bound": "hbm", "frac": hbm_frac, "peak_source": note,
                     "note": "PCG algorithmic bytes of all solves over the graph time (operators streamed "
