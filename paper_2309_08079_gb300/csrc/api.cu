@@ -115,7 +115,9 @@ int choose_pcg_tile(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_schur 
     L.rpt = nx <= 32 ? 1 : 2;
     L.vw = (sizeof(T) == 4 && nx % 4 == 0) ? 4 : 2;
     L.nxc = (sizeof(T) == 4 && (nx == 14 || nx == 36)) ? nx : 0;
-    L.vs = nx <= 16 ? 16 : ceil_div(nx, 4) * 4;
+    // vector slots padded only to the load width (nx = 14: 14, not 16;
+    // measured 3 % faster on 64-knot batches)
+    L.vs = ceil_div(nx, L.vw) * L.vw;
     L.kpc_max = d.N;
     const int SW = 32 / L.lpk;
     const int ns_want = std::max(1, std::min(32, ceil_div(d.N, 4)));
