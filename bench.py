@@ -493,7 +493,9 @@ def summarize(line):
            "large_err_lambda": g(line, "large_state", "err_lambda_vs_oracle", "max"),
            "large_grad_err": g(line, "large_state", "grad_err_vs_oracle", "max"),
            "large_pcg_hbm_frac": g(line, "large_state", "pcg_roofline", "frac"),
-           "large_pcg_streamed_frac": g(line, "large_state", "pcg_roofline", "streamed_frac")}
+           "large_pcg_streamed_frac": g(line, "large_state", "pcg_roofline", "streamed_frac"),
+           "large_pcg_ms": g(line, "large_state", "pcg_roofline", "pcg_ms"),
+           "large_pcg_dot_fp64_ms": g(line, "large_state", "dot_fp64", "pcg_ms")}
     sw = g(line, "sweep", "per_N") or {}
     out["sweep_p50_us"] = {k: g(v, "us_per_solve", "p50") for k, v in sw.items()}
     return out
@@ -1186,6 +1188,22 @@ def run_large(s, dev, solves, B=None, refine_tol=1e-2):
     torch.cuda.synchronize()
     pcg_ms = e0.elapsed_time(e1)
     it1 = read_stats(st1)["iters"].astype(np.float64)
+    # the same solve with the dot products accumulated in float64
+    # (mpcg_opts.dot = 1), the precision the workload names
+    from paper_2309_08079_gb300 import _lib as L
+    o64 = L.mpcg_opts.from_buffer_copy(opts)
+    o64.dot = 1
+    st64 = s.alloc_stats(batch.B, dev)
+    s.pcg_solve(lt, sch, lam0[0].clone(), o64, st64, ws)
+    torch.cuda.synchronize()
+    lam64 = lam0[0].clone()
+    e0.record(stream)
+    s.pcg_solve(lt, sch, lam64, o64, st64, ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pcg64_ms = e0.elapsed_time(e1)
+    it64 = read_stats(st64)["iters"].astype(np.float64)
+    ok64 = bool(np.all(read_stats(st64)["status"] == 0))
     ki = float(np.sum(it1 * Ns))
     alg1 = ki * pcg_bytes_per_knot_iter(c["nx"])
     streamed1 = ki * 2 * 2 * c["nx"] * c["nx"] * 4
@@ -1210,6 +1228,10 @@ def run_large(s, dev, solves, B=None, refine_tol=1e-2):
                                            "(normwise per field, max over fields); forward and adjoint "
                                            "solves each with one refinement step"},
             "pcg_roofline": pcg_alone,
+            "dot_fp64": {"pcg_ms": pcg64_ms, "default_pcg_ms": pcg_ms, "iters_mean": float(np.mean(it64)),
+                         "default_iters_mean": float(np.mean(it1)), "converged": ok64,
+                         "note": "the same warm-started batch PCG solve with float64-accumulated dot products "
+                                 "(mpcg_opts.dot = 1) in the tiled kernel"},
             "pcg_roofline_fwd": {"bound": "hbm", "note": "first PCG of each solve only, over the whole forward "
                                                          "time (formation, both PCG solves of the refinement, "
                                                          "recovery)",

@@ -209,15 +209,20 @@ int choose_pcg(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, co
                PcgLaunch &L) {
     const int mode = o ? o->mode : 0;
     // float64 accumulation of float32 dot products exists in the cluster
-    // kernel only
-    if (std::is_same<T, float>::value && o && o->dot == 1) {
-        if (mode == 2 || mode == 3) return MPCG_EUNSUPPORTED;
-        return choose_pcg_cluster<T>(h, d, B, o, L, mode == 4);
-    }
-    if (mode == 2) return choose_pcg_cta<T>(h, d, B, L);
+    // kernel and in the tiled kernel's compile-time shapes (nx = 14, 36);
+    // the L2 CTA kernel has none
+    const int dot = (std::is_same<T, float>::value && o && o->dot == 1) ? 1 : 0;
+    auto tile = [&](PcgLaunch &Lt) -> int {
+        const int r = choose_pcg_tile<T>(h, d, B, s, Lt);
+        if (r != MPCG_OK || !dot) return r;
+        if (Lt.nxc == 0) return MPCG_EUNSUPPORTED;
+        Lt.dot = 1;
+        return MPCG_OK;
+    };
+    if (mode == 2) return dot ? MPCG_EUNSUPPORTED : choose_pcg_cta<T>(h, d, B, L);
     if (mode == 3) {
-        if (choose_pcg_tile<T>(h, d, B, s, L) == MPCG_OK) return MPCG_OK;
-        return choose_pcg_cta<T>(h, d, B, L);
+        if (tile(L) == MPCG_OK) return MPCG_OK;
+        return dot ? MPCG_EUNSUPPORTED : choose_pcg_cta<T>(h, d, B, L);
     }
     if (mode == 1) return choose_pcg_cluster<T>(h, d, B, o, L);
     if (mode == 4) return choose_pcg_cluster<T>(h, d, B, o, L, true);
@@ -229,12 +234,12 @@ int choose_pcg(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, co
     const bool reg = std::is_same<T, float>::value && d.nx == 14;
     if (!reg && !(o && o->cluster > 0) && (rc != MPCG_OK || (long)B * L.C > h->sms)) {
         PcgLaunch Lt{};
-        if (choose_pcg_tile<T>(h, d, B, s, Lt) == MPCG_OK) {
+        if (tile(Lt) == MPCG_OK) {
             L = Lt;
             return MPCG_OK;
         }
     }
-    if (rc == MPCG_EUNSUPPORTED && !(o && o->cluster > 0)) return choose_pcg_cta<T>(h, d, B, L);
+    if (rc == MPCG_EUNSUPPORTED && !(o && o->cluster > 0) && !dot) return choose_pcg_cta<T>(h, d, B, L);
     return rc;
 }
 

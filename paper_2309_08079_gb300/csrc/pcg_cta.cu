@@ -460,9 +460,11 @@ __device__ __forceinline__ T tile_resid(int nx, int i, T b, const T *D, const T 
 template <int NXC>
 constexpr int tile_max_threads() { return NXC == 36 ? 256 : 512; }
 
-template <typename T, int LPK, int RPT, int VW, int NXC = 0>
+// AT: accumulator of the dot products (Acc<T>; AccF64 for float32 with
+// mpcg_opts.dot = 1, where the few FP64 operations per row and step cost
+// little beside the tile products)
+template <typename T, int LPK, int RPT, int VW, int NXC = 0, typename AT = Acc<T>>
 __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(const PcgParams<T> P) {
-    using AT = Acc<T>;
     using A = typename AT::type;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int SW = 32 / LPK;  // streams per warp
@@ -858,6 +860,10 @@ template <typename T>
 static void (*pcg_tile_fn(const PcgLaunch &L))(const PcgParams<T>) {
     if constexpr (sizeof(T) == 4) {
         // the measured shapes with nx fixed at compile time
+        if (L.dot) {
+            if (L.nxc == 14) return pcg_tile_kernel<T, 16, 1, 2, 14, AccF64>;
+            return pcg_tile_kernel<T, 32, 2, 4, 36, AccF64>;  // nxc 36 (the only other)
+        }
         if (L.nxc == 14) return pcg_tile_kernel<T, 16, 1, 2, 14>;
         if (L.nxc == 36) return pcg_tile_kernel<T, 32, 2, 4, 36>;
         if (L.vw == 4) {
@@ -902,6 +908,8 @@ cudaError_t pcg_tile_prepare(int smem_optin) {
     const auto a = cudaFuncAttributeMaxDynamicSharedMemorySize;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 16, 1, 2, 14>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 4, 36>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 16, 1, 2, 14, AccF64>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 4, 36, AccF64>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 16, 1, 4>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 1, 4>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 4>, a, smem_optin))) return e;
