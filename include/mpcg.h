@@ -149,8 +149,11 @@ typedef struct {
        0 float pairs ("double-float": exact products by FMA, TwoSum
        additions, ~44 significant bits; the default), 1 float64 (products
        and every partial sum in FP64 instructions; slower on GB300, whose
-       FP64 pipe is a small fraction of its FP32 rate).  float64 always
-       accumulates in float64.  Other values: MPCG_EINVAL. */
+       FP64 pipe is a small fraction of its FP32 rate).  1 runs in the
+       cluster kernel and in the tiled kernel for nx = 14 and 36; the L2
+       CTA kernel (mode 2) and other tiled shapes return
+       MPCG_EUNSUPPORTED.  float64 always accumulates in float64.  Other
+       values: MPCG_EINVAL. */
     int dot;
     /* Exit tolerance (relative residual, the correction's own right-hand
        side) of the correction solves of iterative refinement
