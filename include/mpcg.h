@@ -122,7 +122,9 @@ typedef struct {
     /* Batched PCG only: solve just the instances listed (a DEVICE int
        array of n_instances distinct indices into the batch); NULL solves
        all B.  With a list, dims.N may be the largest horizon among the
-       listed instances, which sizes the launch. */
+       listed instances, which sizes the launch.  An entry >= B is skipped
+       (nothing read or written for it, no stats); a negative entry ends
+       the list for the CTA or cluster that draws it. */
     const int *instances;
     int n_instances;
     /* Preconditioner applied by the PCG: 0 the symmetric stair Phi^-1 of

@@ -404,8 +404,13 @@ struct BatchView {
     const int *knot_off;
     int B;
     int N1;
+    // b outside [0, B) (a bad instance-list entry) reads nothing and is an
+    // empty instance
     __device__ __forceinline__ void range(int b, int &k0, int &n) const {
-        if (knot_off) {
+        if (b < 0 || b >= B) {
+            k0 = 0;
+            n = 0;
+        } else if (knot_off) {
             k0 = knot_off[b];
             n = knot_off[b + 1] - k0;
         } else {

@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
         const int k = kfirst + kl;            // this thread's knot
         const bool active_knot = kl < KPC && k < Nb;
         // an instance longer than the launch was sized for is refused
-        const bool bad = (P.info && P.info[b] != 0u) || Nb < 1 || KPC > P.kpc_max;
+        const bool bad = Nb < 1 || (P.info && P.info[b] != 0u) || KPC > P.kpc_max;
         const int max_iter = P.max_iter > 0 ? P.max_iter : 10 * Nb * nx;
         const bool send_left = kl == 0 && has_left;
         const bool send_right = kl == KPC - 1 && has_right;
@@ -700,7 +700,7 @@ __global__ void __launch_bounds__(pcg_max_threads<MODE>(), 1) pcg_cluster_kernel
             for (int m = 0; m < RPT; ++m)
                 if (rv[m]) P.lam[(size_t)(k0 + k) * nx + rows[m]] = lam_r[m];
         }
-        if (rank == 0 && tid == 0 && P.stats) {
+        if (rank == 0 && tid == 0 && P.stats && b < P.bv.B) {
             mpcg_stats st;
             st.iters = iters;
             st.status = status;

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(512, 1) pcg_cta_kernel(const PcgParams<T> P) {
         int k0, Nb;
         P.bv.range(b, k0, Nb);
         const int c0 = k0 - b;
-        const bool bad = (P.info && P.info[b] != 0u) || Nb < 1 || Nb > P.kpc_max;
+        const bool bad = Nb < 1 || (P.info && P.info[b] != 0u) || Nb > P.kpc_max;
         const int max_iter = P.max_iter > 0 ? P.max_iter : 10 * Nb * nx;
         int iters = 0, status = MPCG_CONVERGED;
         A eta = AT::zero(), bb = AT::zero();
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(512, 1) pcg_cta_kernel(const PcgParams<T> P) {
                 P.lam[(size_t)(k0 + k) * nx + i] = vlam[(k + 1) * vs + i];
             }
         }
-        if (tid == 0 && P.stats) {
+        if (tid == 0 && P.stats && b < P.bv.B) {
             mpcg_stats st;
             st.iters = iters;
             st.status = status;
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
         int k0, Nb;
         P.bv.range(b, k0, Nb);
         const int c0 = k0 - b;
-        const bool bad = (P.info && P.info[b] != 0u) || Nb < 1 || Nb > P.kpc_max;
+        const bool bad = Nb < 1 || (P.info && P.info[b] != 0u) || Nb > P.kpc_max;
         const int max_iter = P.max_iter > 0 ? P.max_iter : 10 * Nb * nx;
         int iters = 0, status = MPCG_CONVERGED;
         A eta = AT::zero(), bb = AT::zero();
@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
             }
             if (__syncthreads_or(failed)) failed = true;
         }
-        if (tid == 0 && P.stats) {
+        if (tid == 0 && P.stats && b < P.bv.B) {
             mpcg_stats st;
             st.iters = iters;
             st.status = status;

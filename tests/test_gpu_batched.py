@@ -117,3 +117,33 @@ def test_batched_warm_start():
     lam0 = np.concatenate([gen.warm_start(l, 1500 + i, 0) for i, l in enumerate(los)])
     lam, dx, du, st = _run_batch(batch, lam0=lam0)
     _check(batch, lam, dx, du, st, TOL_F32)
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3])
+def test_out_of_range_instance_entry_is_skipped(mode):
+    """An instance-list entry outside [0, B) reads and writes nothing: the
+    listed in-range instances are solved, the others' lambda and stats stay
+    as they were."""
+    import torch
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    s = solver()
+    Ns = [30, 12, 45]
+    batch = gen.kuka_batch(14, 7, Ns, 3100).astype(np.float32)
+    lt = LQTensors.from_batch(batch)
+    sch = s.alloc_schur(lt)
+    s.form(lt, sch)
+    inst = torch.tensor([0, 7, 2], dtype=torch.int32, device="cuda")
+    lam = torch.full((lt.total, 14), 0.25, device="cuda")
+    stats = s.alloc_stats(lt.nb)
+    stats.fill_(0xFF)
+    s.pcg_solve(lt, sch, lam, make_opts(mode=mode, instances=inst), stats, s.alloc_workspace(lt), N=45)
+    torch.cuda.synchronize()
+    st = read_stats(stats)
+    lam = lam.cpu().double().numpy()
+    ko = batch.knot_off
+    assert st["iters"][1] == -1 and st["status"][1] == -1, st
+    assert np.all(lam[ko[1]:ko[2]] == 0.25)
+    for b in (0, 2):
+        assert st["status"][b] == 0, (b, st[b])
+        lo, _, _ = oracle.kkt_solve(batch.items[b].astype(np.float64))
+        assert oracle.relerr(lam[ko[b]:ko[b + 1]], lo) < TOL_F32, b
