@@ -147,3 +147,45 @@ def test_out_of_range_instance_entry_is_skipped(mode):
         assert st["status"][b] == 0, (b, st[b])
         lo, _, _ = oracle.kkt_solve(batch.items[b].astype(np.float64))
         assert oracle.relerr(lam[ko[b]:ko[b + 1]], lo) < TOL_F32, b
+
+
+def test_tiled_kernel_at_its_largest_horizon():
+    """nx = 36: at the largest horizon the tiled form accepts, the three
+    shared vectors leave room for one knot stream (one warp walking every
+    knot of each pass), and the solve meets the oracle (one refinement
+    step, as at the large-state shape).  One knot more fits no kernel form
+    at nx = 36 (clusters end at 16 CTAs x 16 knots, the L2 CTA kernel's five
+    vectors at ~320 knots): mode 3 and the automatic choice both refuse it
+    with MPCG_EUNSUPPORTED, before any launch."""
+    import torch
+    from paper_2309_08079_gb300._lib import MPCG_EUNSUPPORTED, MPCGError
+    from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
+    s = solver()
+    probe = LQTensors.from_batch(gen.kuka_batch(36, 12, [4, 3], 1).astype(np.float32))
+    psch = s.alloc_schur(probe)
+    o3 = make_opts(mode=3, refine_tol=1e-2)
+
+    def tiled(N):
+        try:
+            return s.pcg_shape(probe, psch, o3, N=N)["form"] == "cta_tma"
+        except MPCGError:
+            return False
+    lo, hi = 64, 1024  # tiled(lo), not tiled(hi)
+    assert tiled(lo) and not tiled(hi)
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        lo, hi = (mid, hi) if tiled(mid) else (lo, mid)
+    Nmax = lo
+    assert 400 <= Nmax <= 486, Nmax
+    batch = gen.kuka_batch(36, 12, [Nmax, 9], 3200 + Nmax).astype(np.float32)
+    lt = LQTensors.from_batch(batch)
+    lam, dx, du, st, sch = s.solve(lt, opts=o3, workspace=s.alloc_workspace(lt), refine=1)
+    sh = s.pcg_shape(lt, sch, o3)
+    assert sh["form"] == "cta_tma" and sh["threads"] == 32, sh
+    torch.cuda.synchronize()
+    lam, dx, du = (t.cpu().double().numpy() for t in (lam, dx, du))
+    _check(batch, lam, dx, du, read_stats(st), TOL_F32)
+    for o in (o3, make_opts()):
+        with pytest.raises(MPCGError) as ei:
+            s.pcg_shape(probe, psch, o, N=Nmax + 1)
+        assert ei.value.code == MPCG_EUNSUPPORTED
