@@ -149,19 +149,21 @@ def test_out_of_range_instance_entry_is_skipped(mode):
         assert oracle.relerr(lam[ko[b]:ko[b + 1]], lo) < TOL_F32, b
 
 
-def test_tiled_kernel_at_its_largest_horizon():
-    """nx = 36: at the largest horizon the tiled form accepts, the three
+@pytest.mark.parametrize("nx,nu,lo_bound,hi_bound", [(36, 12, 400, 486), (14, 7, 1200, 1342)])
+def test_tiled_kernel_at_its_largest_horizon(nx, nu, lo_bound, hi_bound):
+    """At the largest horizon the tiled form accepts, the three
     shared vectors leave room for one knot stream (one warp walking every
-    knot of each pass), and the solve meets the oracle (one refinement
-    step, as at the large-state shape).  One knot more fits no kernel form
-    at nx = 36 (clusters end at 16 CTAs x 16 knots, the L2 CTA kernel's five
-    vectors at ~320 knots): mode 3 and the automatic choice both refuse it
-    with MPCG_EUNSUPPORTED, before any launch."""
+    knot of each pass; two 16-lane streams at nx = 14), and the solve meets
+    the oracle (one refinement step, as at the large-state shape).  One knot
+    more fits no kernel form (clusters end at 16 CTAs x 16 knots at nx = 36
+    and 512 knots at nx = 14, the L2 CTA kernel's five vectors at ~320 and
+    ~724 knots): mode 3 and the automatic choice both refuse it with
+    MPCG_EUNSUPPORTED, before any launch."""
     import torch
     from paper_2309_08079_gb300._lib import MPCG_EUNSUPPORTED, MPCGError
     from paper_2309_08079_gb300.solver import LQTensors, make_opts, read_stats
     s = solver()
-    probe = LQTensors.from_batch(gen.kuka_batch(36, 12, [4, 3], 1).astype(np.float32))
+    probe = LQTensors.from_batch(gen.kuka_batch(nx, nu, [4, 3], 1).astype(np.float32))
     psch = s.alloc_schur(probe)
     o3 = make_opts(mode=3, refine_tol=1e-2)
 
@@ -170,18 +172,18 @@ def test_tiled_kernel_at_its_largest_horizon():
             return s.pcg_shape(probe, psch, o3, N=N)["form"] == "cta_tma"
         except MPCGError:
             return False
-    lo, hi = 64, 1024  # tiled(lo), not tiled(hi)
+    lo, hi = 64, 4096  # tiled(lo), not tiled(hi)
     assert tiled(lo) and not tiled(hi)
     while hi - lo > 1:
         mid = (lo + hi) // 2
         lo, hi = (mid, hi) if tiled(mid) else (lo, mid)
     Nmax = lo
-    assert 400 <= Nmax <= 486, Nmax
-    batch = gen.kuka_batch(36, 12, [Nmax, 9], 3200 + Nmax).astype(np.float32)
+    assert lo_bound <= Nmax <= hi_bound, Nmax
+    batch = gen.kuka_batch(nx, nu, [Nmax, 9], 3200 + Nmax).astype(np.float32)
     lt = LQTensors.from_batch(batch)
     lam, dx, du, st, sch = s.solve(lt, opts=o3, workspace=s.alloc_workspace(lt), refine=1)
     sh = s.pcg_shape(lt, sch, o3)
-    assert sh["form"] == "cta_tma" and sh["threads"] == 32, sh
+    assert sh["form"] == "cta_tma" and sh["threads"] == 32, sh  # one warp
     torch.cuda.synchronize()
     lam, dx, du = (t.cpu().double().numpy() for t in (lam, dx, du))
     _check(batch, lam, dx, du, read_stats(st), TOL_F32)
