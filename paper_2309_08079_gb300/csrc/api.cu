@@ -246,6 +246,7 @@ int choose_pcg(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, co
 template <typename T>
 int form_schur_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const mpcg_lq *lq,
                  mpcg_schur *s, cudaStream_t st) {
+    (void)h;  // formation needs no handle state (the signature matches the other calls)
     SchurArgs<T> a;
     a.nx = d.nx;
     a.nu = d.nu;
