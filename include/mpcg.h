@@ -66,7 +66,7 @@ extern "C" {
 #define MPCG_EINVAL (-1)       /* bad argument (null pointer, size, dtype) */
 #define MPCG_ECUDA (-2)        /* a CUDA runtime call or launch failed */
 #define MPCG_EUNSUPPORTED (-3) /* shape outside what the kernels support (float32: horizons
-                                  up to ~1,340 knots at nx = 14, ~480 at nx = 36; every
+                                  up to ~1,340 knots at nx = 14, ~500 at nx = 36; every
                                   form keeps an instance's vectors on chip) */
 #define MPCG_ETOOLARGE (-4)    /* needs more scratch than MPCG_NOALLOC_SCRATCH_BYTES */
 
@@ -101,6 +101,17 @@ typedef struct {
 typedef struct {
     void *Sd, *So, *Pd, *Po, *gamma;
     unsigned int *info; /* device, one word per instance, or NULL */
+    /* Optional packed copies of the symmetric diagonal blocks for the tiled
+       PCG kernel at nx = 36 (float32): Sdp[K][npk], Pdp[K][npk] hold the
+       upper triangles of Sd[k] and Pd[k] column by column (entry (i, j),
+       i <= j, at j (j + 1) / 2 + i), npk = nx (nx + 1) / 2 rounded up to a
+       multiple of 4, zero-padded; 16-byte aligned, caller-owned.  When both
+       are non-NULL, mpcg_form_precon[_batched] and
+       mpcg_form_schur_precon[_batched] write them after Pd, and the tiled
+       kernel streams them instead of Sd and Pd (666 of 1,296 words per
+       block); entry (j, i) is read as (i, j).  A caller that changes Sd or Pd
+       after formation must form again or pass NULL.  NULL: unused. */
+    void *Sdp, *Pdp;
 } mpcg_schur;
 
 typedef struct {

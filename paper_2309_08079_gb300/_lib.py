@@ -57,7 +57,8 @@ class mpcg_lq_out(C.Structure):
 
 
 class mpcg_schur(C.Structure):
-    _fields_ = [(n, C.c_void_p) for n in ("Sd", "So", "Pd", "Po", "gamma")] + [("info", C.c_void_p)]
+    _fields_ = [(n, C.c_void_p) for n in ("Sd", "So", "Pd", "Po", "gamma")] + [("info", C.c_void_p)] + \
+        [(n, C.c_void_p) for n in ("Sdp", "Pdp")]
 
 
 class mpcg_opts(C.Structure):

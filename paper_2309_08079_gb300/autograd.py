@@ -42,17 +42,18 @@ class MPCGSolve(torch.autograd.Function):
         ctx.opts = bopts
         ctx.workspace = cfg.get("workspace")
         ctx.save_for_backward(lq.A, lq.B, lq.Qd, lq.Rd, lq.q, lq.r, lq.c, schur.Sd, schur.So,
-                              schur.Pd, schur.Po, schur.gamma, schur.info, lam, dx, du)
+                              schur.Pd, schur.Po, schur.gamma, schur.info, lam, dx, du, schur.Sdp,
+                              schur.Pdp)
         ctx.fwd_stats = stats
         ctx.mark_non_differentiable(stats)
         return lam, dx, du, stats
 
     @staticmethod
     def backward(ctx, g_lam, g_dx, g_du, _g_stats):
-        (A, B, Qd, Rd, q, r, c, Sd, So, Pd, Po, gamma, info, lam, dx, du) = ctx.saved_tensors
+        (A, B, Qd, Rd, q, r, c, Sd, So, Pd, Po, gamma, info, lam, dx, du, Sdp, Pdp) = ctx.saved_tensors
         nx, nu, N, knot_off, nb, total = ctx.lq_meta
         lq = LQTensors(nx, nu, N, A, B, Qd, Rd, q, r, c, knot_off=knot_off, nb=nb, total=total)
-        schur = SchurTensors(Sd, So, Pd, Po, gamma, info)
+        schur = SchurTensors(Sd, So, Pd, Po, gamma, info, Sdp, Pdp)
         z = lambda t, like: (t.contiguous() if t is not None else torch.zeros_like(like))
         g, stats = ctx.solver.backward(lq, schur, lam, dx, du, z(g_lam, lam), z(g_dx, dx),
                                        z(g_du, du), opts=ctx.opts, workspace=ctx.workspace)

@@ -121,18 +121,41 @@ int choose_pcg_tile(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_schur 
     L.kpc_max = d.N;
     const int SW = 32 / L.lpk;
     const int ns_want = std::max(1, std::min(32, ceil_div(d.N, 4)));
-    int bestW = 0, bestD = 0;
     const int wmax = L.nxc == 36 ? 8 : 16;  // the nx = 36 form is compiled for <= 256 threads
-    for (int W = std::min(wmax, ceil_div(ns_want, SW)); W >= 1 && !bestW; --W)
-        for (int dep = 2; dep >= 1; --dep)
-            if (pcg_tile_smem_bytes<T>(d.N, L.vs, W, W * SW, nx, dep) <= (size_t)h->smem_optin) {
-                bestW = W;
-                bestD = dep;
-                break;
-            }
+    // the most streams (then the deepest ring) that fit, with diagonal slots
+    // of npk entries (0: full tiles)
+    auto fit = [&](int npk_, int &W_, int &D_) {
+        W_ = D_ = 0;
+        for (int W = std::min(wmax, ceil_div(ns_want, SW)); W >= 1 && !W_; --W)
+            for (int dep = 2; dep >= 1; --dep)
+                if (pcg_tile_smem_bytes<T>(d.N, L.vs, W, W * SW, nx, dep, npk_) <= (size_t)h->smem_optin) {
+                    W_ = W;
+                    D_ = dep;
+                    break;
+                }
+    };
+    int bestW = 0, bestD = 0;
+    fit(0, bestW, bestD);
+    // Packed diagonal blocks (nx = 36, when the caller formed them) cut the
+    // bytes per step by a quarter but add a scalar load per entry: taken
+    // only when their smaller slots fit more knot streams (long horizons,
+    // where the kernel is bound by bytes in flight; measured 1.16-1.21x at
+    // N = 160-256, 5 % slower at N = 64 where the streams are capped anyway).
+    L.pk = 0;
+    int npk = 0;
+    if (L.nxc == 36 && s->Sdp && s->Pdp && (((uintptr_t)s->Sdp | (uintptr_t)s->Pdp) % 16) == 0) {
+        int pW = 0, pD = 0;
+        fit(packed_len(nx), pW, pD);
+        if (pW > bestW) {
+            L.pk = 1;
+            npk = packed_len(nx);
+            bestW = pW;
+            bestD = pD;
+        }
+    }
     if (!bestW) return MPCG_EUNSUPPORTED;
     L.depth = bestD;
-    L.smem = pcg_tile_smem_bytes<T>(d.N, L.vs, bestW, bestW * SW, nx, bestD);
+    L.smem = pcg_tile_smem_bytes<T>(d.N, L.vs, bestW, bestW * SW, nx, bestD, npk);
     L.threads = 32 * bestW;
     const int per_sm = pcg_tile_max_blocks<T>(L);
     if (per_sm < 1) return MPCG_EUNSUPPORTED;
@@ -274,10 +297,12 @@ int pcg_shape_t(mpcg_handle *h, const mpcg_dims &d, int B, const mpcg_opts *o, c
     std::lock_guard<std::mutex> g(h->mu);
     // the tiled kernel's eligibility depends on pointer alignment
     const int aligned = (((uintptr_t)s->Sd | (uintptr_t)s->So | (uintptr_t)s->Pd | (uintptr_t)s->Po) % 16) == 0;
+    // packed diagonal blocks change the tiled kernel's shared-memory layout
+    const int packed = (s->Sdp && s->Pdp && (((uintptr_t)s->Sdp | (uintptr_t)s->Pdp) % 16) == 0) ? 1 : 0;
     const int tickets = (o && o->instances && o->n_instances > 0) ? o->n_instances : B;
     auto key = std::make_tuple(d.dtype, d.nx, d.N, tickets,
                                (o ? o->cluster : 0) | ((o ? o->mode : 0) << 8) | (aligned << 16) |
-                                   ((o ? o->dot : 0) << 17));
+                                   ((o ? o->dot : 0) << 17) | (packed << 18));
     auto it = h->shapes.find(key);
     if (it != h->shapes.end()) {
         L = it->second;
@@ -313,6 +338,9 @@ int pcg_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const 
     if (P.precon < 0 || P.precon > 2) return MPCG_EINVAL;
     P.inst_list = (o && o->instances && o->n_instances > 0) ? o->instances : nullptr;
     P.n_tickets = P.inst_list ? o->n_instances : B;
+    P.Sdp = (L.cta_mode == 2 && L.pk) ? (const T *)s->Sdp : nullptr;
+    P.Pdp = (L.cta_mode == 2 && L.pk) ? (const T *)s->Pdp : nullptr;
+    P.npk = packed_len(d.nx);
     if (P.inst_list && !knot_off) return MPCG_EINVAL;
     if (P.n_tickets > 1 && L.clusters < P.n_tickets) {
         if (!ws) return MPCG_EINVAL;
@@ -379,11 +407,25 @@ template <typename T>
 int form_all_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, const mpcg_lq *lq,
                mpcg_schur *s, cudaStream_t st);
 
+// The packed diagonal blocks, when the caller provides them (after Sd and Pd
+// are final).
+template <typename T>
+int pack_t(const mpcg_dims &d, int B, const int *knot_off, mpcg_schur *s, cudaStream_t st) {
+    if (!s->Sdp || !s->Pdp) return MPCG_OK;
+    if ((((uintptr_t)s->Sdp | (uintptr_t)s->Pdp) % 16) != 0) return MPCG_EINVAL;
+    const BatchView bv = make_bv(knot_off, B, d.N);
+    const int Kgrid = knot_off ? B * d.N : d.N, npk = packed_len(d.nx);
+    int rc = err_cuda(launch_pack_diag<T>(d.nx, npk, bv, Kgrid, (const T *)s->Sd, (T *)s->Sdp, st));
+    if (rc) return rc;
+    return err_cuda(launch_pack_diag<T>(d.nx, npk, bv, Kgrid, (const T *)s->Pd, (T *)s->Pdp, st));
+}
+
 template <typename T>
 int precon_t(const mpcg_dims &d, int B, const int *knot_off, mpcg_schur *s, cudaStream_t st) {
-    return err_cuda(launch_form_precon<T>(d.nx, make_bv(knot_off, B, d.N), knot_off ? B * d.N : d.N,
-                                          (const T *)s->Sd, (const T *)s->So, (T *)s->Pd,
-                                          (T *)s->Po, st));
+    const int rc = err_cuda(launch_form_precon<T>(d.nx, make_bv(knot_off, B, d.N), knot_off ? B * d.N : d.N,
+                                                  (const T *)s->Sd, (const T *)s->So, (T *)s->Pd,
+                                                  (T *)s->Po, st));
+    return rc ? rc : pack_t<T>(d, B, knot_off, s, st);
 }
 
 template <typename T>
@@ -413,7 +455,8 @@ int form_all_t(mpcg_handle *h, const mpcg_dims &d, int B, const int *knot_off, c
         int e = err_cuda(cudaMemsetAsync(s->info, 0, sizeof(unsigned) * B, st));
         if (e) return e;
     }
-    return err_cuda(launch_form_fused<T>(a, (T *)s->Pd, (T *)s->Po, h->sms, st));
+    const int rc = err_cuda(launch_form_fused<T>(a, (T *)s->Pd, (T *)s->Po, h->sms, st));
+    return rc ? rc : pack_t<T>(d, B, knot_off, s, st);
 }
 
 template <typename T>

@@ -997,6 +997,34 @@ cudaError_t launch_axpy(int nx, BatchView bv, int Kgrid, const T *d, T *lam, cud
     return cudaGetLastError();
 }
 
+// Packed copy of the symmetric diagonal blocks: Dp[k] holds the upper
+// triangle of D[k] column by column (entry (i, j), i <= j, at j (j + 1) / 2
+// + i) and zeros up to npk.  One thread per packed entry of one knot.
+template <typename T>
+__global__ void pack_diag_kernel(int nx, int npk, BatchView bv, const T *__restrict__ D, T *__restrict__ Dp) {
+    const size_t n = (size_t)bv.total() * npk;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t k = e / npk;
+        const int p = (int)(e % npk);
+        T v = T(0);
+        if (p < nx * (nx + 1) / 2) {
+            int j = 0;  // column j holds entries [j (j + 1) / 2, (j + 1) (j + 2) / 2)
+            while ((j + 1) * (j + 2) / 2 <= p) ++j;
+            const int i = p - j * (j + 1) / 2;
+            v = D[k * nx * nx + (size_t)i * nx + j];
+        }
+        Dp[e] = v;
+    }
+}
+
+template <typename T>
+cudaError_t launch_pack_diag(int nx, int npk, BatchView bv, int Kgrid, const T *D, T *Dp, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = std::max(1, std::min(4096, ceil_div(Kgrid * npk, threads)));
+    pack_diag_kernel<T><<<blocks, threads, 0, s>>>(nx, npk, bv, D, Dp);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_zero(int nx, BatchView bv, int Kgrid, T *v, cudaStream_t s) {
     const int threads = 256;
@@ -1046,6 +1074,7 @@ cudaError_t form_prepare(int smem_optin) {
                                          T, const T *, T *, cudaStream_t);                        \
     template cudaError_t launch_axpy<T>(int, BatchView, int, const T *, T *, cudaStream_t);     \
     template cudaError_t launch_zero<T>(int, BatchView, int, T *, cudaStream_t);                 \
+    template cudaError_t launch_pack_diag<T>(int, int, BatchView, int, const T *, T *, cudaStream_t); \
     template cudaError_t launch_form_fused<T>(const SchurArgs<T> &, T *, T *, int, cudaStream_t); \
     template size_t form_fused_smem_bytes<T>(int, int, int, int);                                \
     template cudaError_t launch_recover_dense<T>(int, int, BatchView, int, const T *, const T *, \

@@ -39,6 +39,8 @@ struct PcgParams {
     int stage_smem;   // PTR mode: stage blocks in shared memory
     int vs;           // shared vector stride (elements per knot)
     int depth;        // pcg_tile_kernel: steps each knot stream copies ahead
+    const T *Sdp, *Pdp;  // pcg_tile_kernel: packed diagonal blocks (nullptr: full Sd, Pd)
+    int npk;             // entries per packed diagonal block
 };
 
 struct PcgLaunch {
@@ -52,6 +54,7 @@ struct PcgLaunch {
     int vw;        // pcg_tile_kernel: elements per shared-memory row load (2 or 4)
     int depth;     // pcg_tile_kernel: steps each knot stream copies ahead (1..4)
     int nxc;       // pcg_tile_kernel: nx fixed at compile time (14, 36), else 0
+    int pk;        // pcg_tile_kernel: streams the packed diagonal blocks (nx = 36)
     int dot;       // float32 only: 1 accumulates the dot products in float64 (AccF64)
     size_t smem;
 };
@@ -84,12 +87,17 @@ template <typename T>
 cudaError_t launch_axpy(int nx, BatchView bv, int Kgrid, const T *d, T *lam, cudaStream_t s);
 template <typename T>
 cudaError_t launch_zero(int nx, BatchView bv, int Kgrid, T *v, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pack_diag(int nx, int npk, BatchView bv, int Kgrid, const T *D, T *Dp, cudaStream_t s);
+// entries per packed diagonal block: nx(nx+1)/2 rounded up to 4 (16 bytes)
+__host__ __device__ __forceinline__ int packed_len(int nx) { return (nx * (nx + 1) / 2 + 3) / 4 * 4; }
 template <typename T> cudaError_t pcg_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
 template <typename T> int pcg_max_clusters(const PcgLaunch &);
 cudaError_t pcg_prepare(int smem_optin);
 cudaError_t pcg_cta_prepare(int smem_optin);
 cudaError_t pcg_tile_prepare(int smem_optin);
-template <typename T> size_t pcg_tile_smem_bytes(int nmax, int vs, int W, int NS, int nx, int depth);
+template <typename T>
+size_t pcg_tile_smem_bytes(int nmax, int vs, int W, int NS, int nx, int depth, int npk);
 template <typename T> cudaError_t pcg_tile_launch(const PcgLaunch &, const PcgParams<T> &, cudaStream_t);
 template <typename T> int pcg_tile_max_blocks(const PcgLaunch &);
 template <typename T> size_t pcg_cta_smem_bytes(int nmax, int vs, int W);

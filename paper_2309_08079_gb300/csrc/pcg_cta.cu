@@ -276,14 +276,14 @@ __global__ void __launch_bounds__(512, 1) pcg_cta_kernel(const PcgParams<T> P) {
 // symmetric, so reading row i of D_k gives the same products, in the same
 // order, as reading its column i.
 // ---------------------------------------------------------------------------
-// Per knot stream and pipeline depth d: a ring of d+1 diagonal-block tiles,
-// d+1 off-diagonal tiles and d+1 mbarriers.
-__host__ __device__ constexpr int tile_slots(int depth) { return 2 * depth + 2; }
+// Per knot stream and pipeline depth d: a ring of d+1 diagonal-block slots
+// (full or packed blocks), d+1 off-diagonal tiles and d+1 mbarriers.
 
 template <typename T>
 struct TileLayout {
-    size_t r, p, w, tiles, tile_bytes, stream_bytes, mbar, wpart, misc, total;
-    __host__ __device__ TileLayout(int nmax, int vs, int W, int NS, int nx, int depth) {
+    size_t r, p, w, tiles, tile_bytes, dtile_bytes, stream_bytes, mbar, wpart, misc, total;
+    // npk > 0: the diagonal slots hold packed blocks of npk entries
+    __host__ __device__ TileLayout(int nmax, int vs, int W, int NS, int nx, int depth, int npk) {
         using A = typename std::conditional<sizeof(T) == 4, dfloat, double>::type;
         auto al = [](size_t x) { return (x + 127) & ~size_t(127); };
         size_t o = 0;
@@ -292,7 +292,8 @@ struct TileLayout {
         p = o; o = al(o + v);
         w = o; o = al(o + v);
         tile_bytes = (sizeof(T) * (size_t)nx * nx + 15) & ~size_t(15);
-        stream_bytes = (size_t)tile_slots(depth) * tile_bytes;
+        dtile_bytes = npk > 0 ? (sizeof(T) * (size_t)npk + 15) & ~size_t(15) : tile_bytes;
+        stream_bytes = (size_t)(depth + 1) * (dtile_bytes + tile_bytes);
         // Two 16-lane streams share a warp when nx <= 16; their rings are
         // padded to 64 bytes past a multiple of 128, so the two half-warps'
         // column reads of their upper blocks (14 consecutive words each,
@@ -329,11 +330,17 @@ __device__ __forceinline__ void vload(const T *p, T (&o)[VW]) {
 // stream's next step uses while O_k's slot is already being refilled.  Each
 // block's products go to two accumulators (even and odd columns), each in
 // column order.  nx % VW == 0.
-template <typename T, int VW, int RPT, int LPK, bool HU, bool HN>
+// Entry (i, j) of a packed symmetric block (upper triangle by columns:
+// (i, j), i <= j, at j (j + 1) / 2 + i; (j, i) is the same entry).
+__host__ __device__ __forceinline__ int packed_index(int i, int j) {
+    return i <= j ? j * (j + 1) / 2 + i : i * (i + 1) / 2 + j;
+}
+
+template <typename T, int VW, int RPT, int LPK, bool HU, bool HN, bool PK, int ND>
 __device__ __forceinline__ void tile_cols(int nx, int j, int li, const bool (&ok)[RPT], const T *D,
                                           const T *O, const T *vself, const T *vnext, T (&a0)[RPT],
                                           T (&a2)[RPT], T (&b0)[RPT], T (&b2)[RPT], T (&c1)[RPT],
-                                          T (&d1)[RPT]) {
+                                          T (&d1)[RPT], const int (&doff)[ND]) {
     T xs[VW], xn[VW];
     vload<T, VW>(vself + j, xs);
     if (HU) vload<T, VW>(vnext + j, xn);
@@ -342,7 +349,15 @@ __device__ __forceinline__ void tile_cols(int nx, int j, int li, const bool (&ok
         if (ok[m]) {
             const int i = li + m * LPK;
             T d[VW], l[VW];
-            vload<T, VW>(D + i * nx + j, d);
+            if constexpr (PK) {
+                // row li of the packed block: consecutive words up to the
+                // diagonal's column, a per-lane stride past it (offsets
+                // computed once per launch)
+#pragma unroll
+                for (int t = 0; t < VW; ++t) d[t] = D[doff[j + t]];
+            } else {
+                vload<T, VW>(D + i * nx + j, d);
+            }
             if (HN) vload<T, VW>(O + i * nx + j, l);
 #pragma unroll
             for (int t = 0; t < VW; t += 2) {  // even columns into a / c, odd into b / d
@@ -365,11 +380,11 @@ __device__ __forceinline__ void tile_cols(int nx, int j, int li, const bool (&ok
 // cl / dl / ts).  Sum: ((D_e + D_o) + (L_e + L_o)) + (U_e + U_o), the even
 // / odd column split halving the chains (measured 1-2 % faster).  NXC > 0
 // fixes nx at compile time (the column loop unrolls completely).
-template <typename T, int VW, int RPT, int LPK, int NXC>
+template <typename T, int VW, int RPT, int LPK, int NXC, bool PK, int ND>
 __device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T *O, bool hu, bool hn,
                                           const T *Lg, bool lc, const T *vprev, const T *vself,
                                           const T *vnext, T (&y)[RPT], T (&cl)[RPT], T (&dl)[RPT],
-                                          T &ts) {
+                                          T &ts, const int (&doff)[ND]) {
     const int nx = NXC > 0 ? NXC : nx_rt;
     // nx fixed a little above a warp (nx = 36): the 4 rows past the first 32
     // are split over the whole warp, 8 lanes per row with a strided subset
@@ -391,11 +406,13 @@ __device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T
         if constexpr (NXC > 0) {
 #pragma unroll
             for (int j = 0; j < NXC; j += VW)
-                tile_cols<T, VW, RPT, LPK, HU, HN>(nx, j, li, ok, D, O, vself, vnext, a0, a2, b0, b2, c1, d1);
+                tile_cols<T, VW, RPT, LPK, HU, HN, PK, ND>(nx, j, li, ok, D, O, vself, vnext, a0, a2, b0, b2,
+                                                            c1, d1, doff);
         } else {
 #pragma unroll 2
             for (int j = 0; j < nx; j += VW)
-                tile_cols<T, VW, RPT, LPK, HU, HN>(nx, j, li, ok, D, O, vself, vnext, a0, a2, b0, b2, c1, d1);
+                tile_cols<T, VW, RPT, LPK, HU, HN, PK, ND>(nx, j, li, ok, D, O, vself, vnext, a0, a2, b0, b2,
+                                                            c1, d1, doff);
         }
     };
     using Y = std::true_type;
@@ -425,7 +442,7 @@ __device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T
         for (int q = 0; q < (NXC + 7) / 8; ++q) {
             const int j = g + 8 * q;
             if (live && j < NXC) {
-                t0 = fma_rn(D[row * NXC + j], vself[j], t0);
+                t0 = fma_rn(PK ? D[packed_index(row, j)] : D[row * NXC + j], vself[j], t0);
                 if (Lg) t1 = fma_rn(Lg[row * NXC + j], vprev[j], t1);
                 if (hu) t2 = fma_rn(O[j * NXC + row], vnext[j], t2);
                 if (hn) tn = fma_rn(O[row * NXC + j], vself[j], tn);
@@ -442,11 +459,12 @@ __device__ __forceinline__ void tile_rows(int nx_rt, int li, const T *D, const T
 
 // b_i - (row i) . v with exact products and an extended sum (as resid_ptr)
 template <typename T>
-__device__ __forceinline__ T tile_resid(int nx, int i, T b, const T *D, const T *Lg, const T *U,
+__device__ __forceinline__ T tile_resid(int nx, int i, T b, const T *D, bool packed, const T *Lg, const T *U,
                                         const T *vprev, const T *vself, const T *vnext) {
     using AT = Acc<T>;
     typename AT::type a = AT::prod(b, T(1));
-    for (int j = 0; j < nx; ++j) a = AT::add(a, AT::prod(-D[i * nx + j], vself[j]));
+    for (int j = 0; j < nx; ++j)
+        a = AT::add(a, AT::prod(-(packed ? D[packed_index(i, j)] : D[i * nx + j]), vself[j]));
     if (Lg)
         for (int j = 0; j < nx; ++j) a = AT::add(a, AT::prod(-__ldg(Lg + i * nx + j), vprev[j]));
     if (U)
@@ -463,8 +481,11 @@ constexpr int tile_max_threads() { return NXC == 36 ? 256 : 512; }
 // AT: accumulator of the dot products (Acc<T>; AccF64 for float32 with
 // mpcg_opts.dot = 1, where the few FP64 operations per row and step cost
 // little beside the tile products)
-template <typename T, int LPK, int RPT, int VW, int NXC = 0, typename AT = Acc<T>>
+template <typename T, int LPK, int RPT, int VW, int NXC = 0, typename AT = Acc<T>, bool PK = false>
 __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(const PcgParams<T> P) {
+    // PK: the diagonal blocks arrive packed (upper triangle by columns) and
+    // are read in place, each lane through its row's 36 offsets
+    static_assert(!PK || (NXC == 36 && LPK == 32 && RPT == 2), "packed blocks: the nx = 36 form");
     using A = typename AT::type;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int SW = 32 / LPK;  // streams per warp
@@ -476,10 +497,15 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
     const int li = lane % LPK;
     const bool leader = li == 0;
     const int nx = NXC > 0 ? NXC : P.nx, vs = P.vs, nx2 = nx * nx;
+    // packed blocks: this lane's row li at column j is entry doff[j]
+    constexpr int ND = PK ? NXC : 1;
+    int doff[ND];
+#pragma unroll
+    for (int j = 0; j < ND; ++j) doff[j] = packed_index(li, j);
     const uint32_t nxb = (uint32_t)(nx2 * sizeof(T));
     const int depth = P.depth;       // steps copied ahead
     const int RD = depth + 1, RO = depth + 1, RM = depth + 1;  // ring sizes
-    TileLayout<T> Lo(P.kpc_max, vs, W, NS, nx, depth);
+    TileLayout<T> Lo(P.kpc_max, vs, W, NS, nx, depth, PK ? P.npk : 0);
     T *vr = reinterpret_cast<T *>(smem + Lo.r);
     T *vp = reinterpret_cast<T *>(smem + Lo.p);
     T *vw = reinterpret_cast<T *>(smem + Lo.w);
@@ -547,7 +573,10 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
         int i_d = 0, i_o = 0, i_m = 0;  // its D slot, O slot, barrier
         int c_d = 0, c_o = 0, c_m = 0;  // next step to consume: D slot, O slot, barrier
         auto wrap = [](int x, int n) { return x + 1 == n ? 0 : x + 1; };
-        auto tile = [&](int slot) { return reinterpret_cast<T *>(tb + (size_t)slot * Lo.tile_bytes); };
+        auto dslot = [&](int slot) { return reinterpret_cast<T *>(tb + (size_t)slot * Lo.dtile_bytes); };
+        auto oslot = [&](int slot) {
+            return reinterpret_cast<T *>(tb + (size_t)RD * Lo.dtile_bytes + (size_t)slot * Lo.tile_bytes);
+        };
         // the copies of the next step to issue (leader lane; len > 0): even
         // passes read S+, odd passes Phi^-1
         auto issue_next = [&]() {
@@ -558,9 +587,15 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
             // block Jacobi passes (odd, Phi^-1) use no off-diagonal blocks; a
             // stair pass needs O_k in row k (k odd) or in row k + 1 (k even)
             const bool hasU = k + 1 < Nb && !((i_ps & 1) && P.precon == 1);
-            mbar_arrive_expect(bar, hasU ? 2u * nxb : nxb);
-            bulk_g2s(smem_u32(tile(i_d)), Md + (size_t)(k0 + k) * nx2, nxb, bar);
-            if (hasU) bulk_g2s(smem_u32(tile(RD + i_o)), Mo + (size_t)(c0 + k) * nx2, nxb, bar);
+            const uint32_t db = PK ? (uint32_t)(P.npk * sizeof(T)) : nxb;
+            mbar_arrive_expect(bar, hasU ? db + nxb : db);
+            if constexpr (PK) {
+                const T *Mp = (i_ps & 1) ? P.Pdp : P.Sdp;
+                bulk_g2s(smem_u32(dslot(i_d)), Mp + (size_t)(k0 + k) * P.npk, db, bar);
+            } else {
+                bulk_g2s(smem_u32(dslot(i_d)), Md + (size_t)(k0 + k) * nx2, nxb, bar);
+            }
+            if (hasU) bulk_g2s(smem_u32(oslot(i_o)), Mo + (size_t)(c0 + k) * nx2, nxb, bar);
         };
         auto advance_issue = [&]() {
             if (++i_t == len) {
@@ -634,9 +669,9 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
                 if (act) {
                     const int k = ks0 + t;
                     const bool off = offd(k);
-                    const T *D = tile(c_d);
+                    const T *D = dslot(c_d);
                     // O_k was copied when some row uses it (as in issue_next)
-                    const T *O = (k + 1 < Nb && !((ps & 1) && P.precon == 1)) ? tile(RD + c_o) : nullptr;
+                    const T *O = (k + 1 < Nb && !((ps & 1) && P.precon == 1)) ? oslot(c_o) : nullptr;
                     const bool hu = off && k + 1 < Nb;
                     advance_use();
                     if (kind == 0) {
@@ -648,7 +683,7 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
                             const int i = li + m * LPK;
                             if (i < nx) {
                                 const T bi = P.rhs_sign * P.rhs[(size_t)(k0 + k) * nx + i];
-                                out[(k + 1) * vs + i] = tile_resid<T>(nx, i, bi, D, Lg, hu ? O : nullptr, v + k * vs,
+                                out[(k + 1) * vs + i] = tile_resid<T>(nx, i, bi, D, PK, Lg, hu ? O : nullptr, v + k * vs,
                                                                       v + (k + 1) * vs, v + (k + 2) * vs);
                                 dot = AT::add(dot, AT::prod(bi, bi));
                             }
@@ -661,8 +696,9 @@ __global__ void __launch_bounds__(tile_max_threads<NXC>(), 1) pcg_tile_kernel(co
                         // row k+1's, for this stream's next step
                         const bool hn = t + 1 < len && k + 1 < Nb && offd(k + 1);
                         T y[RPT];
-                        tile_rows<T, VW, RPT, LPK, NXC>(nx, li, D, O, hu, hn, Lg, lc, v + k * vs,
-                                                        v + (k + 1) * vs, v + (k + 2) * vs, y, cl, dl, ts);
+                        tile_rows<T, VW, RPT, LPK, NXC, PK, ND>(nx, li, D, O, hu, hn, Lg, lc, v + k * vs,
+                                                                v + (k + 1) * vs, v + (k + 2) * vs, y, cl, dl,
+                                                                ts, doff);
 #pragma unroll
                         for (int m = 0; m < RPT; ++m) {
                             const int i = li + m * LPK;
@@ -860,6 +896,9 @@ template <typename T>
 static void (*pcg_tile_fn(const PcgLaunch &L))(const PcgParams<T>) {
     if constexpr (sizeof(T) == 4) {
         // the measured shapes with nx fixed at compile time
+        if (L.nxc == 36 && L.pk)
+            return L.dot ? pcg_tile_kernel<T, 32, 2, 4, 36, AccF64, true>
+                         : pcg_tile_kernel<T, 32, 2, 4, 36, Acc<T>, true>;
         if (L.dot) {
             if (L.nxc == 14) return pcg_tile_kernel<T, 16, 1, 2, 14, AccF64>;
             return pcg_tile_kernel<T, 32, 2, 4, 36, AccF64>;  // nxc 36 (the only other)
@@ -878,8 +917,8 @@ static void (*pcg_tile_fn(const PcgLaunch &L))(const PcgParams<T>) {
 }
 
 template <typename T>
-size_t pcg_tile_smem_bytes(int nmax, int vs, int W, int NS, int nx, int depth) {
-    return TileLayout<T>(nmax, vs, W, NS, nx, depth).total;
+size_t pcg_tile_smem_bytes(int nmax, int vs, int W, int NS, int nx, int depth, int npk) {
+    return TileLayout<T>(nmax, vs, W, NS, nx, depth, npk).total;
 }
 
 template <typename T>
@@ -910,6 +949,8 @@ cudaError_t pcg_tile_prepare(int smem_optin) {
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 4, 36>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 16, 1, 2, 14, AccF64>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 4, 36, AccF64>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 4, 36, Acc<float>, true>, a, smem_optin))) return e;
+    if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 4, 36, AccF64, true>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 16, 1, 4>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 1, 4>, a, smem_optin))) return e;
     if ((e = cudaFuncSetAttribute(pcg_tile_kernel<float, 32, 2, 4>, a, smem_optin))) return e;
@@ -921,8 +962,8 @@ cudaError_t pcg_tile_prepare(int smem_optin) {
     return cudaFuncSetAttribute(pcg_tile_kernel<double, 32, 2, 2>, a, smem_optin);
 }
 
-template size_t pcg_tile_smem_bytes<float>(int, int, int, int, int, int);
-template size_t pcg_tile_smem_bytes<double>(int, int, int, int, int, int);
+template size_t pcg_tile_smem_bytes<float>(int, int, int, int, int, int, int);
+template size_t pcg_tile_smem_bytes<double>(int, int, int, int, int, int, int);
 template cudaError_t pcg_tile_launch<float>(const PcgLaunch &, const PcgParams<float> &, cudaStream_t);
 template cudaError_t pcg_tile_launch<double>(const PcgLaunch &, const PcgParams<double> &, cudaStream_t);
 template int pcg_tile_max_blocks<float>(const PcgLaunch &);

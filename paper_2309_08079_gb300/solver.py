@@ -100,6 +100,11 @@ class LQTensors:
                          **LQTensors._dense(batch.lq, device, dtype))
 
 
+def packed_len(nx: int) -> int:
+    """Entries per packed diagonal block: nx(nx+1)/2 rounded up to 4."""
+    return (nx * (nx + 1) // 2 + 3) // 4 * 4
+
+
 @dataclass
 class SchurTensors:
     Sd: torch.Tensor
@@ -108,10 +113,13 @@ class SchurTensors:
     Po: torch.Tensor
     gamma: torch.Tensor
     info: torch.Tensor
+    Sdp: Optional[torch.Tensor] = None  # packed upper triangles of Sd, Pd ([K][packed_len(nx)])
+    Pdp: Optional[torch.Tensor] = None
 
     def struct(self) -> L.mpcg_schur:
+        pk = [None if t is None else t.data_ptr() for t in (self.Sdp, self.Pdp)]
         return L.mpcg_schur(*(t.data_ptr() for t in (self.Sd, self.So, self.Pd, self.Po,
-                                                      self.gamma, self.info)))
+                                                      self.gamma, self.info)), *pk)
 
 
 def make_opts(tol=1e-6, tol_mode=0, max_iter=0, cluster=0, mode=0, instances=None,
@@ -159,13 +167,19 @@ class Solver:
             pass
 
     # ---------------------------------------------------------------- buffers
-    def alloc_schur(self, lq: LQTensors) -> SchurTensors:
+    def alloc_schur(self, lq: LQTensors, packed: Optional[bool] = None) -> SchurTensors:
+        """S+, Phi^-1 and gamma buffers.  packed (default: float32 batches at
+        nx = 36, where the tiled kernel is bound by HBM bandwidth) adds the
+        packed diagonal blocks the tiled kernel streams instead of Sd, Pd."""
         nx, K, dt, dev = lq.nx, lq.total, lq.dtype, lq.device
         Kc = K - lq.nb
         e = lambda *s: torch.empty(*s, dtype=dt, device=dev)
+        if packed is None:
+            packed = lq.batched and dt == torch.float32 and nx == 36
+        pk = (e(K, packed_len(nx)), e(K, packed_len(nx))) if packed else (None, None)
         return SchurTensors(e(K, nx, nx), e(max(Kc, 1), nx, nx), e(K, nx, nx),
                             e(max(Kc, 1), nx, nx), e(K, nx),
-                            torch.zeros(lq.nb, dtype=torch.int32, device=dev))
+                            torch.zeros(lq.nb, dtype=torch.int32, device=dev), *pk)
 
     def alloc_stats(self, nb: int = 1, device=None) -> torch.Tensor:
         return torch.zeros(nb * L.STATS_BYTES, dtype=torch.uint8,
