@@ -1206,15 +1206,22 @@ def run_large(s, dev, solves, B=None, refine_tol=1e-2):
     ok64 = bool(np.all(read_stats(st64)["status"] == 0))
     ki = float(np.sum(it1 * Ns))
     alg1 = ki * pcg_bytes_per_knot_iter(c["nx"])
-    streamed1 = ki * 2 * 2 * c["nx"] * c["nx"] * 4
+    # bytes the tiled kernel copies per knot and pass: the diagonal block
+    # (packed upper triangle when the launch streams it) and O_k
+    sh1 = s.pcg_shape(lt, sch, opts)
+    nx_ = c["nx"]
+    dwords = ((nx_ * (nx_ + 1) // 2 + 3) // 4 * 4) if sh1.get("packed") else nx_ * nx_
+    streamed1 = ki * 2 * (dwords + nx_ * nx_) * 4
     pcg_alone = {"bound": "hbm", "pcg_ms": pcg_ms, "plan": best["plan"],
                  "achieved": alg1 / (pcg_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                  "frac": alg1 / (pcg_ms / 1e3) / 1e9 / hbm, "peak_source": note,
                  "streamed_gbs": streamed1 / (pcg_ms / 1e3) / 1e9,
                  "streamed_frac": streamed1 / (pcg_ms / 1e3) / 1e9 / hbm,
+                 "shape": sh1,
                  "note": "one warm-started PCG solve of the whole batch timed alone; achieved = algorithmic "
                          "bytes (symmetric diagonal blocks, (2T + 7 nx) x 4 B per knot-iteration); streamed = "
-                         "the full tiles the kernel copies (diagonal and off-diagonal block per knot and pass)"}
+                         "the tiles the kernel copies (diagonal block, packed when shape.packed, and "
+                         "off-diagonal block per knot and pass)"}
     return {"workload": f"{batch.B} instances, nx={c['nx']}, nu={c['nu']}, N_i ~ U{{{c['N_lo']}..{c['N_hi']}}} "
                         f"(sum {int(ko[-1])} knots), {solves} warm solves per step + backward, one refinement "
                         f"step after the forward and after the adjoint solve (corrections to {refine_tol:g})",

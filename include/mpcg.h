@@ -264,9 +264,12 @@ int mpcg_pcg_solve(mpcg_handle *h, mpcg_dims dims, const mpcg_schur *schur, void
  * shape[0] = kernel form (0 a thread-block cluster per instance, 1 one CTA
  * per instance reading the blocks from L2, 2 the tiled kernel streaming
  * TMA tiles), shape[1] = CTAs per cluster, shape[2] = clusters (or CTAs) in
- * the grid, shape[3] = threads per CTA.  `shape` is a HOST int[4]; the
- * schur pointers matter only through their alignment (the tiled kernel
- * needs 16-byte-aligned blocks).  B = 1 for a single instance.
+ * the grid, shape[3] = threads per CTA, shape[4] = tiled kernel: steps each
+ * knot stream copies ahead (else 0), shape[5] = tiled kernel: 1 if it
+ * streams the packed diagonal blocks (schur->Sdp, Pdp), else 0.  `shape` is
+ * a HOST int[6]; the schur pointers matter only through their alignment
+ * (the tiled kernel needs 16-byte-aligned blocks) and whether the packed
+ * copies are given.  B = 1 for a single instance.
  */
 int mpcg_pcg_shape(mpcg_handle *h, mpcg_dims dims, int B, const mpcg_schur *schur,
                    const mpcg_opts *opts, int *shape);

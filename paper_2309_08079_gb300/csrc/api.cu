@@ -641,6 +641,8 @@ int mpcg_pcg_shape(mpcg_handle *h, mpcg_dims d, int B, const mpcg_schur *s, cons
     shape[1] = L.C;
     shape[2] = L.clusters;
     shape[3] = L.threads;
+    shape[4] = L.cta_mode == 2 ? L.depth : 0;
+    shape[5] = L.cta_mode == 2 ? L.pk : 0;
     return MPCG_OK;
 }
 

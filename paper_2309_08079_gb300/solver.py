@@ -201,10 +201,10 @@ class Solver:
         dims = lq.dims()
         if N is not None:
             dims.N = int(N)
-        shape = (C.c_int * 4)()
+        shape = (C.c_int * 6)()
         L.check("mpcg_pcg_shape", self.lib.mpcg_pcg_shape(self.h, dims, lq.nb, C.byref(ss), C.byref(o), shape))
         return {"form": ("cluster", "cta_l2", "cta_tma")[shape[0]], "C": shape[1], "clusters": shape[2],
-                "threads": shape[3]}
+                "threads": shape[3], "depth": shape[4], "packed": bool(shape[5])}
 
     def bench_exchange(self, C_: int, W: int, rounds: int = 2000, stream=None) -> dict:
         """Latency of one cluster reduction of the PCG kernels (both of

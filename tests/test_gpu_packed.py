@@ -69,8 +69,9 @@ def test_packed_blocks_taken_when_they_fit_more_streams():
     sp, sf = s.alloc_schur(lt, packed=True), s.alloc_schur(lt, packed=False)
     long_p, long_f = s.pcg_shape(lt, sp, o, N=256), s.pcg_shape(lt, sf, o, N=256)
     assert long_p["threads"] > long_f["threads"], (long_p, long_f)
+    assert long_p["packed"] and not long_f["packed"]
     short_p, short_f = s.pcg_shape(lt, sp, o, N=16), s.pcg_shape(lt, sf, o, N=16)
-    assert short_p == short_f, (short_p, short_f)
+    assert short_p == short_f and not short_p["packed"], (short_p, short_f)
 
 
 def test_packed_solve_meets_oracle():
