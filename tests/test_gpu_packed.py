@@ -109,3 +109,39 @@ def test_packed_ignored_by_other_kernels():
         lp, _ = _pcg(s, lt, sp, mode)
         lf, _ = _pcg(s, lt, sf, mode)
         np.testing.assert_array_equal(lp, lf)
+
+
+def test_packed_blocks_with_the_comparison_preconditioners():
+    """The packed path under opts.precon 1 (block Jacobi: Pd alone in the
+    Phi^-1 passes) and 2 (the non-symmetric stair: Pd alone at even knots):
+    after a fixed number of iterations lambda equals the oracle's Algorithm 1
+    iterate with the same preconditioner, instance by instance, on a batch
+    long enough that the launch takes the packed blocks."""
+    import torch
+    from paper_2309_08079_gb300.solver import make_opts, read_stats
+    m = 10
+    batch, s, lt = _setup([256, 33, 190], 4536)
+    sch = s.alloc_schur(lt)
+    s.form(lt, sch)
+    ko = batch.knot_off
+    for precon in (1, 2):
+        o = make_opts(mode=3, precon=precon, tol=1e-30, max_iter=m)
+        assert s.pcg_shape(lt, sch, o)["packed"]
+        lam = torch.zeros(lt.total, 36, device="cuda")
+        st = s.alloc_stats(lt.nb)
+        s.pcg_solve(lt, sch, lam, o, st)
+        torch.cuda.synchronize()
+        st = read_stats(st)
+        lam = lam.cpu().double().numpy()
+        for b, it in enumerate(batch.items):
+            Sd, So, g = oracle.schur_blocks(it.astype(np.float64))
+            S = oracle.block_tridiag_sparse(Sd, So)
+            if precon == 1:
+                Pd, _ = oracle.precon_blocks(Sd, So)
+                Pm = oracle.block_tridiag_sparse(Pd, np.zeros_like(So))
+            else:
+                Pm = oracle.stair_inverse(Sd, So)
+            lo, its, _ = oracle.pcg_op(S, Pm, -g, tol=1e-30, max_iter=m)
+            assert its == m and st["status"][b] == 1 and st["iters"][b] == m, (precon, b, st[b])
+            e = oracle.relerr(lam[ko[b]:ko[b + 1]], lo.reshape(-1, 36))
+            assert e < 1e-3, (precon, b, e)
