@@ -274,7 +274,9 @@ __global__ void __launch_bounds__(512, 1) pcg_cta_kernel(const PcgParams<T> P) {
 // the scalars.  Only the first knot of a range reads its lower block from
 // global memory directly (once per pass).  The diagonal blocks are exactly
 // symmetric, so reading row i of D_k gives the same products, in the same
-// order, as reading its column i.
+// order, as reading its column i -- and at nx = 36 the launch may stream
+// only their upper triangles (packed by columns, read in place) when the
+// smaller slots fit more knot streams.
 // ---------------------------------------------------------------------------
 // Per knot stream and pipeline depth d: a ring of d+1 diagonal-block slots
 // (full or packed blocks), d+1 off-diagonal tiles and d+1 mbarriers.
